@@ -1,0 +1,241 @@
+/*
+ * gblod.h -- C ABI of the GB300-native level-of-detail particle renderer.
+ *
+ * Method: Szalay, Springel & Lemson, "GPU-Based Interactive Visualization of Billion Point
+ * Cosmological Simulations" (arXiv:0811.2055).  The paper's three requirements -- simplify
+ * the data into visually equivalent levels of detail, index them spatially, and let the
+ * renderer decide per view what to draw -- become two calls:
+ *
+ *   gblod_build_lod(particles, masses, n_max) -> octree      (octree paragraph)
+ *   gblod_render(octree, camera, resolution)  -> image       (depth and GPU paragraphs)
+ *
+ * plus a brute-force render of every particle (the "full rendering" the LOD image must be
+ * indistinguishable from, abstract).  Every computation runs in the library's sm_103a CUDA
+ * kernels; this header has no CUDA or torch types.
+ *
+ * Conventions for every call below:
+ *   - Pointers named d_* are device pointers (cudaMalloc / torch CUDA tensors) on the current
+ *     CUDA device; h_* are host pointers.  Caller-owned buffers are only read or written by
+ *     work enqueued on `stream` during the call, so they must stay valid until that work is
+ *     done.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - Arguments are checked on the host before anything is enqueued; on any error the
+ *     out-parameters are left untouched and nothing has been written.
+ *   - Device-side checks (fixed-point range) set a sticky status word in the renderer that
+ *     gblod_renderer_status() returns; the device never traps or waits without a bound.
+ *   - Errors: gblod_status codes; gblod_last_error() gives a message for the calling thread.
+ */
+#ifndef GBLOD_H
+#define GBLOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBLOD_OK = 0,
+    GBLOD_ERR_INVALID_ARG = 1,   /* a pointer, size or parameter is invalid */
+    GBLOD_ERR_RANGE = 2,         /* a mass, or a fixed-point amplitude / sum, is out of range */
+    GBLOD_ERR_OOM = 3,           /* the allocator returned NULL */
+    GBLOD_ERR_CUDA = 4,          /* a CUDA runtime call failed (message in gblod_last_error) */
+    GBLOD_ERR_DEVICE_TIMEOUT = 5,/* a bounded device wait ran out */
+    GBLOD_ERR_NOT_IMPLEMENTED = 6
+} gblod_status;
+
+/* ----------------------------------------------------------------- memory */
+/* Optional allocation hook (e.g. the torch caching allocator).  alloc returns device memory
+ * usable on `stream` or NULL; free releases it after the work already enqueued on `stream`.
+ * A NULL gblod_allocator* (or NULL alloc) selects cudaMallocAsync / cudaFreeAsync. */
+typedef void *(*gblod_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*gblod_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+typedef struct {
+    gblod_alloc_fn alloc;
+    gblod_free_fn free;
+    void *ctx;
+} gblod_allocator;
+
+/* ----------------------------------------------------------------- octree */
+#define GBLOD_NODE_LEAF 1u     /* stores its particles verbatim */
+#define GBLOD_NODE_INTERNAL 2u /* has children */
+#define GBLOD_NODE_LOSSY 4u    /* depth-21 node holding more than n_max particles */
+#define GBLOD_NODE_REPS 8u     /* stores n_max representatives (INTERNAL or LOSSY) */
+#define GBLOD_MAX_DEPTH 21
+
+/* Octree build parameters (octree paragraph: "at most n points (in our case, n=16000)"). */
+typedef struct {
+    uint64_t seed;        /* keys the counter-based generator of the subselection */
+    uint32_t n_max;       /* at most n_max points per node; >= 1 */
+    uint32_t reserved;
+    double root_lo[3];    /* root cube [root_lo, root_lo + root_side)^3; finite */
+    double root_side;     /* > 0 and finite */
+} gblod_build_params;
+
+/* One node of the octree, breadth-first order (depth, then locational code).  112 bytes. */
+typedef struct {
+    uint64_t code;        /* locational code (1 << 3*depth) | octant path */
+    uint64_t seg_first;   /* first position in the (key, id)-sorted particle order */
+    uint64_t point_first; /* first stored point in the packed point arrays */
+    uint64_t mass_lo;     /* exact node mass: sum of mass * 2^47, low 64 bits */
+    uint64_t mass_hi;     /* ... high 64 bits */
+    uint32_t seg_count;   /* particles inside the node */
+    uint32_t point_count; /* stored points: seg_count for leaves, n_max otherwise */
+    uint32_t child_first; /* index of the first child (0 if none) */
+    uint32_t child_count; /* non-empty octants */
+    int32_t depth;
+    int32_t flags;        /* GBLOD_NODE_* */
+    int32_t parent;       /* -1 for the root */
+    int32_t pad;
+    float h_cull;         /* largest smoothing length drawn anywhere in the subtree */
+    float w_rep;          /* weight of each representative, fp32(M_node / n_max); 0 for leaves */
+    float s_rep;          /* smoothing-length scale of the representatives; 1 for leaves */
+    float pad2;
+    float bmin[3];        /* bounds of the node's particles */
+    float bmax[3];
+} gblod_node;
+
+typedef struct gblod_octree gblod_octree; /* opaque, device resident, library owned */
+
+typedef struct {
+    uint64_t n_particles;
+    uint64_t n_nodes;
+    uint64_t n_points;    /* stored points over all nodes */
+    uint64_t device_bytes;
+    int32_t depth_max;
+    int32_t equal_mass;   /* 1 if every particle had the same mass (raw draws are the keys) */
+    uint32_t n_max;
+    uint32_t reserved;
+} gblod_octree_info;
+
+/* Builds the octree on the device (octree paragraph; A1 Morton keys, A2 radix sort, A3 node
+ * counting, A4 density-weighted subselection, A5 representatives).
+ *   d_xyz   n x 3 float32 positions (row-major), d_mass n float32 in [2^-24, 2^24], d_h n
+ *           float32 smoothing lengths; d_ids NULL (particle id = input index) or n distinct
+ *           uint32 ids that key the generator (so a permutation of rows with their ids gives
+ *           the same tree); n < 2^32.
+ *   Memory for the octree comes from `alloc` (kept by the octree and used again to free it).
+ *   The call synchronises `stream` a few times (the host needs the node counts) and returns
+ *   when the octree is complete.  GBLOD_ERR_RANGE if a mass is outside [2^-24, 2^24] or not
+ *   finite. */
+gblod_status gblod_build_lod(const float *d_xyz, const float *d_mass, const float *d_h, const uint32_t *d_ids,
+                             uint64_t n, const gblod_build_params *params, const gblod_allocator *alloc,
+                             void *stream, gblod_octree **out);
+
+/* Frees the octree (after work already enqueued on the build's allocator stream semantics:
+ * the caller must make sure no render using it is still running). */
+void gblod_octree_free(gblod_octree *octree);
+
+gblod_status gblod_octree_get_info(const gblod_octree *octree, gblod_octree_info *out);
+
+/* Copies octree arrays to host buffers (each may be NULL; sizes from gblod_octree_get_info):
+ *   h_nodes n_nodes gblod_node; h_pts4 n_points x 4 float (x, y, z, weight); h_hs n_points
+ *   float; h_pt_src n_points uint32 (sorted position each stored point copies); h_skey
+ *   n_particles uint64 sorted Morton keys; h_sidx n_particles uint32 input index per sorted
+ *   position.  Synchronous. */
+gblod_status gblod_octree_export(const gblod_octree *octree, gblod_node *h_nodes, float *h_pts4, float *h_hs,
+                                 uint32_t *h_pt_src, uint64_t *h_skey, uint32_t *h_sidx);
+
+/* ----------------------------------------------------------------- rendering */
+/* Pinhole camera (depth paragraph; GPU paragraph).  right/up/fwd are orthonormal rows;
+ * image coordinates: u = cx + f_px * x_c / z_c, v = cy - f_px * y_c / z_c (y points down);
+ * points with z_c <= z_near are not drawn.  width, height in 1..16384. */
+typedef struct {
+    double eye[3], right[3], up[3], fwd[3];
+    double f_px, cx, cy, z_near;
+    int32_t width, height;
+} gblod_camera;
+
+#define GBLOD_KERNEL_GAUSSIAN 0 /* truncated at 3 sigma, sigma = h */
+#define GBLOD_KERNEL_CUBIC 1    /* M4 cubic spline with support 2h (the paper's "radial cubic") */
+
+typedef struct {
+    double lambda_px;     /* detail threshold: refine while (f * edge)^2 > lambda^2 max(D^2, z_near^2);
+                             negative selects the default sqrt(n_max) */
+    double sigma_min_px;  /* blob size clamp in pixels, 0 < min <= max (default 0.5, 128) */
+    double sigma_max_px;
+    double tone_lo, tone_hi; /* fixed log range in intensity units (used when tone_auto == 0) */
+    int32_t kernel;       /* GBLOD_KERNEL_* */
+    int32_t tone_auto;    /* 1: hi = image maximum, lo = 1e-4 hi */
+    int32_t tile_w, tile_h; /* screen tile in pixels (0 = 16); any value gives the same image */
+} gblod_render_params;
+
+/* Render workspace: scratch buffers (grown on demand through the allocator), the sticky
+ * device status word and the last frame's counters.  One renderer must not be used by two
+ * calls that overlap on the device. */
+typedef struct gblod_renderer gblod_renderer;
+
+gblod_status gblod_renderer_create(const gblod_allocator *alloc, gblod_renderer **out);
+void gblod_renderer_destroy(gblod_renderer *r);
+
+/* LOD frame (R1 node selection, R2 projection and binning, R3 tiled splat, R4 tone map).
+ *   d_image  height x width uint8 (row-major) or NULL; d_accum height x width uint64
+ *   fixed-point intensities (2^-32 units) or NULL (then an internal buffer is used).
+ *   Enqueued on `stream`; the call waits once on `stream` mid-frame to size the splat lists. */
+gblod_status gblod_render(gblod_renderer *r, const gblod_octree *octree, const gblod_camera *camera,
+                          const gblod_render_params *params, uint8_t *d_image, uint64_t *d_accum, void *stream);
+
+/* Brute-force frame: R2-R4 over every particle (d_xyz n x 3, d_mass n, d_h n), no tree. */
+gblod_status gblod_render_bruteforce(gblod_renderer *r, const float *d_xyz, const float *d_mass, const float *d_h,
+                                     uint64_t n, const gblod_camera *camera, const gblod_render_params *params,
+                                     uint8_t *d_image, uint64_t *d_accum, void *stream);
+
+typedef struct {
+    uint64_t nodes_selected; /* R1 output */
+    uint64_t points;         /* points fed to R2 */
+    uint64_t splats;         /* points drawn after culling */
+    uint64_t pairs;          /* (tile, splat) records */
+    uint64_t tiles;
+    uint64_t amplitude_lo, amplitude_hi; /* sum of drawn amplitudes */
+} gblod_frame_stats;
+
+/* Waits for `stream`, then reports the sticky device status (GBLOD_OK or GBLOD_ERR_RANGE /
+ * GBLOD_ERR_DEVICE_TIMEOUT) and, if reset != 0, clears it. */
+gblod_status gblod_renderer_status(gblod_renderer *r, void *stream, int reset);
+
+/* Counters of the last frame; waits for `stream`. */
+gblod_status gblod_renderer_stats(gblod_renderer *r, void *stream, gblod_frame_stats *out);
+
+/* Node indices selected by the last LOD frame (any order), up to `cap`; *count gets the total.
+ * Waits for `stream`. */
+gblod_status gblod_renderer_last_selection(gblod_renderer *r, void *stream, uint32_t *h_nodes, uint64_t cap,
+                                           uint64_t *count);
+
+/* ----------------------------------------------------------------- stage entry points */
+/* A1 alone: 63-bit Morton keys of n points (octree paragraph; q = clamp(floor((x - lo) 2^21 /
+ * side)), octant bits (x<<2)|(y<<1)|z, level 1 in bits 62..60). */
+gblod_status gblod_morton_keys(const float *d_xyz, uint64_t n, const double root_lo[3], double root_side,
+                               uint64_t *d_keys, void *stream);
+
+/* R2 alone, for n points given as float4 (x, y, z, weight) + h: d_out n x 5 int64 =
+ * {drawn (1), culled (0) or out of range (-1), U, V, S, Wq}. */
+gblod_status gblod_project(const float *d_pts4, const float *d_h, uint64_t n, const gblod_camera *camera,
+                           const gblod_render_params *params, int64_t *d_out, void *stream);
+
+/* ----------------------------------------------------------------- instrumentation */
+/* Number of kernel launches this library has issued in the process. */
+uint64_t gblod_launch_count(void);
+
+/* Kernel ids for the timing probe. */
+typedef enum {
+    GBLOD_K_ANY = 0,
+    GBLOD_K_MORTON, GBLOD_K_SORT_UPSWEEP, GBLOD_K_SORT_SCATTER, GBLOD_K_SCAN, GBLOD_K_BUILD_OTHER,
+    GBLOD_K_SEL_HIST, GBLOD_K_SEL_MARK, GBLOD_K_SEL_WRITE, GBLOD_K_SELECT_NODES, GBLOD_K_PROJECT_COUNT,
+    GBLOD_K_PROJECT_SCATTER, GBLOD_K_SPLAT, GBLOD_K_TONEMAP, GBLOD_K_RENDER_OTHER,
+    GBLOD_K_COUNT_
+} gblod_kernel_id;
+
+/* Timing probe: while enabled for `kernel` (GBLOD_K_ANY = none), every launch of that kernel is
+ * bracketed by CUDA events on its own stream.  gblod_probe_read waits for the recorded events
+ * and returns the summed device time and the number of launches since the probe was enabled. */
+gblod_status gblod_probe_enable(int32_t kernel);
+gblod_status gblod_probe_read(double *total_ms, uint64_t *launches);
+
+const char *gblod_status_string(gblod_status s);
+const char *gblod_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBLOD_H */

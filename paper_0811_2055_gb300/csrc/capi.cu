@@ -1,0 +1,262 @@
+// The C ABI declared in include/gblod.h: host-side argument checks, then the device work.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "render.cuh"
+
+using namespace gb;
+
+namespace {
+
+template <class F> gblod_status guarded(F &&f)
+{
+    try {
+        f();
+        return GBLOD_OK;
+    } catch (const Error &e) {
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return GBLOD_ERR_OOM;
+    } catch (...) {
+        set_error("unexpected exception");
+        return GBLOD_ERR_CUDA;
+    }
+}
+
+bool finite3(const double v[3]) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+void check_camera(const gblod_camera *c)
+{
+    if (!c) fail(GBLOD_ERR_INVALID_ARG, "camera is NULL");
+    if (!finite3(c->eye) || !finite3(c->right) || !finite3(c->up) || !finite3(c->fwd) || !std::isfinite(c->f_px) ||
+        !std::isfinite(c->cx) || !std::isfinite(c->cy) || !std::isfinite(c->z_near))
+        fail(GBLOD_ERR_INVALID_ARG, "camera fields must be finite");
+    if (!(c->f_px > 0.0) || !(c->z_near >= 0.0)) fail(GBLOD_ERR_INVALID_ARG, "camera needs f_px > 0, z_near >= 0");
+    if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384)
+        fail(GBLOD_ERR_INVALID_ARG, "camera width/height must be in 1..16384");
+}
+
+gblod_render_params check_params(const gblod_render_params *p)
+{
+    if (!p) fail(GBLOD_ERR_INVALID_ARG, "render params are NULL");
+    gblod_render_params q = *p;
+    if (!(q.sigma_min_px > 0.0) || !(q.sigma_max_px >= q.sigma_min_px) || !std::isfinite(q.sigma_max_px))
+        fail(GBLOD_ERR_INVALID_ARG, "need 0 < sigma_min_px <= sigma_max_px < inf");
+    if ((float)q.sigma_max_px > 4096.0f) fail(GBLOD_ERR_INVALID_ARG, "sigma_max_px must be <= 4096");
+    if (q.kernel != GBLOD_KERNEL_GAUSSIAN && q.kernel != GBLOD_KERNEL_CUBIC)
+        fail(GBLOD_ERR_INVALID_ARG, "unknown kernel");
+    if (std::isnan(q.lambda_px)) fail(GBLOD_ERR_INVALID_ARG, "lambda_px is NaN");
+    if (q.tile_w == 0) q.tile_w = 16;
+    if (q.tile_h == 0) q.tile_h = 16;
+    if (q.tile_w < 1 || q.tile_h < 1 || q.tile_w > 64 || q.tile_h > 64 || q.tile_w * q.tile_h > 4096)
+        fail(GBLOD_ERR_INVALID_ARG, "tile must be 1..64 x 1..64 with at most 4096 pixels");
+    if (!q.tone_auto && !(q.tone_hi > q.tone_lo && q.tone_lo > 0.0 && std::isfinite(q.tone_hi)))
+        fail(GBLOD_ERR_INVALID_ARG, "fixed tone range needs 0 < tone_lo < tone_hi < inf");
+    return q;
+}
+
+} // namespace
+
+extern "C" {
+
+gblod_status gblod_build_lod(const float *d_xyz, const float *d_mass, const float *d_h, const uint32_t *d_ids,
+                             uint64_t n, const gblod_build_params *params, const gblod_allocator *alloc,
+                             void *stream, gblod_octree **out)
+{
+    return guarded([&] {
+        if (!out || !params) fail(GBLOD_ERR_INVALID_ARG, "out and params must not be NULL");
+        if (n > 0 && (!d_xyz || !d_mass || !d_h)) fail(GBLOD_ERR_INVALID_ARG, "particle arrays must not be NULL");
+        if (n >= 0xFFFFFFFFull) fail(GBLOD_ERR_INVALID_ARG, "n must be below 2^32 - 1");
+        if (params->n_max < 1) fail(GBLOD_ERR_INVALID_ARG, "n_max must be >= 1");
+        if (!finite3(params->root_lo) || !(params->root_side > 0.0) || !std::isfinite(params->root_side))
+            fail(GBLOD_ERR_INVALID_ARG, "root cube must be finite with side > 0");
+        Allocator A(alloc);
+        *out = build_octree(d_xyz, d_mass, d_h, d_ids, n, *params, A, (cudaStream_t)stream);
+    });
+}
+
+void gblod_octree_free(gblod_octree *octree)
+{
+    if (!octree) return;
+    (void)cudaStreamSynchronize(octree->stream);
+    free_octree(octree);
+    (void)cudaGetLastError();
+}
+
+gblod_status gblod_octree_get_info(const gblod_octree *o, gblod_octree_info *out)
+{
+    if (!o || !out) {
+        set_error("octree and out must not be NULL");
+        return GBLOD_ERR_INVALID_ARG;
+    }
+    gblod_octree_info i;
+    std::memset(&i, 0, sizeof(i));
+    i.n_particles = o->n;
+    i.n_nodes = o->n_nodes;
+    i.n_points = o->n_points;
+    i.device_bytes = o->bytes;
+    i.depth_max = o->depth_max;
+    i.equal_mass = o->equal_mass;
+    i.n_max = o->n_max;
+    *out = i;
+    return GBLOD_OK;
+}
+
+gblod_status gblod_octree_export(const gblod_octree *o, gblod_node *h_nodes, float *h_pts4, float *h_hs,
+                                 uint32_t *h_pt_src, uint64_t *h_skey, uint32_t *h_sidx)
+{
+    return guarded([&] {
+        if (!o) fail(GBLOD_ERR_INVALID_ARG, "octree is NULL");
+        cudaStream_t s = o->stream;
+        if (h_nodes && o->n_nodes)
+            GB_CUDA(cudaMemcpyAsync(h_nodes, o->nodes, o->n_nodes * sizeof(gblod_node), cudaMemcpyDeviceToHost, s));
+        if (h_pts4 && o->n_points)
+            GB_CUDA(cudaMemcpyAsync(h_pts4, o->pts4, o->n_points * sizeof(float4), cudaMemcpyDeviceToHost, s));
+        if (h_hs && o->n_points)
+            GB_CUDA(cudaMemcpyAsync(h_hs, o->hs, o->n_points * sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (h_pt_src && o->n_points)
+            GB_CUDA(cudaMemcpyAsync(h_pt_src, o->pt_src, o->n_points * 4, cudaMemcpyDeviceToHost, s));
+        if (h_skey && o->n) GB_CUDA(cudaMemcpyAsync(h_skey, o->skey, o->n * 8, cudaMemcpyDeviceToHost, s));
+        if (h_sidx && o->n) GB_CUDA(cudaMemcpyAsync(h_sidx, o->sidx, o->n * 4, cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+gblod_status gblod_renderer_create(const gblod_allocator *alloc, gblod_renderer **out)
+{
+    return guarded([&] {
+        if (!out) fail(GBLOD_ERR_INVALID_ARG, "out is NULL");
+        gblod_renderer *r = new gblod_renderer();
+        r->A = Allocator(alloc);
+        try {
+            renderer_init(r, nullptr);
+        } catch (...) {
+            delete r;
+            throw;
+        }
+        *out = r;
+    });
+}
+
+void gblod_renderer_destroy(gblod_renderer *r)
+{
+    if (!r) return;
+    try {
+        renderer_release(r);
+    } catch (...) {
+    }
+    delete r;
+    (void)cudaGetLastError();
+}
+
+gblod_status gblod_render(gblod_renderer *r, const gblod_octree *octree, const gblod_camera *camera,
+                          const gblod_render_params *params, uint8_t *d_image, uint64_t *d_accum, void *stream)
+{
+    return guarded([&] {
+        if (!r || !octree) fail(GBLOD_ERR_INVALID_ARG, "renderer and octree must not be NULL");
+        check_camera(camera);
+        const gblod_render_params p = check_params(params);
+        render_lod(r, octree, *camera, p, d_image, d_accum, (cudaStream_t)stream);
+    });
+}
+
+gblod_status gblod_render_bruteforce(gblod_renderer *r, const float *d_xyz, const float *d_mass, const float *d_h,
+                                     uint64_t n, const gblod_camera *camera, const gblod_render_params *params,
+                                     uint8_t *d_image, uint64_t *d_accum, void *stream)
+{
+    return guarded([&] {
+        if (!r) fail(GBLOD_ERR_INVALID_ARG, "renderer is NULL");
+        if (n > 0 && (!d_xyz || !d_mass || !d_h)) fail(GBLOD_ERR_INVALID_ARG, "particle arrays must not be NULL");
+        check_camera(camera);
+        const gblod_render_params p = check_params(params);
+        render_brute(r, d_xyz, d_mass, d_h, n, *camera, p, d_image, d_accum, (cudaStream_t)stream);
+    });
+}
+
+gblod_status gblod_renderer_status(gblod_renderer *r, void *stream, int reset)
+{
+    gblod_status out = GBLOD_OK;
+    gblod_status st = guarded([&] {
+        if (!r) fail(GBLOD_ERR_INVALID_ARG, "renderer is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        unsigned *h = static_cast<unsigned *>(r->hs.get(16));
+        unsigned long long *amp = reinterpret_cast<unsigned long long *>(h + 2);
+        GB_CUDA(cudaMemcpyAsync(h, r->status, 4, cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaMemcpyAsync(amp, &r->stats->amp_hi, 8, cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        unsigned bits = h[0];
+        if (*amp) bits |= 1u;
+        if (reset) GB_CUDA(cudaMemsetAsync(r->status, 0, 4, s));
+        if (bits & 2u)
+            out = GBLOD_ERR_DEVICE_TIMEOUT;
+        else if (bits & 1u)
+            out = GBLOD_ERR_RANGE;
+        if (reset) GB_CUDA(cudaStreamSynchronize(s));
+    });
+    return st != GBLOD_OK ? st : out;
+}
+
+gblod_status gblod_renderer_stats(gblod_renderer *r, void *stream, gblod_frame_stats *out)
+{
+    return guarded([&] {
+        if (!r || !out) fail(GBLOD_ERR_INVALID_ARG, "renderer and out must not be NULL");
+        FrameStatsDev *h = static_cast<FrameStatsDev *>(r->hs.get(sizeof(FrameStatsDev)));
+        GB_CUDA(cudaMemcpyAsync(h, r->stats, sizeof(FrameStatsDev), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+        GB_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+        out->nodes_selected = h->nodes_selected;
+        out->points = h->points;
+        out->splats = h->splats;
+        out->pairs = h->pairs;
+        out->tiles = h->tiles;
+        out->amplitude_lo = h->amp_lo;
+        out->amplitude_hi = h->amp_hi;
+    });
+}
+
+gblod_status gblod_renderer_last_selection(gblod_renderer *r, void *stream, uint32_t *h_nodes, uint64_t cap,
+                                           uint64_t *count)
+{
+    return guarded([&] {
+        if (!r || !count) fail(GBLOD_ERR_INVALID_ARG, "renderer and count must not be NULL");
+        if (!r->last_was_lod || !r->sel.p) {
+            *count = 0;
+            return;
+        }
+        FrameStatsDev *h = static_cast<FrameStatsDev *>(r->hs.get(sizeof(FrameStatsDev)));
+        GB_CUDA(cudaMemcpyAsync(h, r->stats, sizeof(FrameStatsDev), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+        GB_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+        const uint64_t n = h->nodes_selected;
+        *count = n;
+        const uint64_t m = n < cap ? n : cap;
+        if (h_nodes && m) {
+            GB_CUDA(cudaMemcpyAsync(h_nodes, r->sel.p, m * 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+            GB_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+        }
+    });
+}
+
+gblod_status gblod_morton_keys(const float *d_xyz, uint64_t n, const double root_lo[3], double root_side,
+                               uint64_t *d_keys, void *stream)
+{
+    return guarded([&] {
+        if (n > 0 && (!d_xyz || !d_keys)) fail(GBLOD_ERR_INVALID_ARG, "arrays must not be NULL");
+        if (!root_lo || !finite3(root_lo) || !(root_side > 0.0) || !std::isfinite(root_side))
+            fail(GBLOD_ERR_INVALID_ARG, "root cube must be finite with side > 0");
+        if (n) morton_keys(d_xyz, n, root_lo, root_side, d_keys, (cudaStream_t)stream);
+    });
+}
+
+gblod_status gblod_project(const float *d_pts4, const float *d_h, uint64_t n, const gblod_camera *camera,
+                           const gblod_render_params *params, int64_t *d_out, void *stream)
+{
+    return guarded([&] {
+        if (n > 0 && (!d_pts4 || !d_h || !d_out)) fail(GBLOD_ERR_INVALID_ARG, "arrays must not be NULL");
+        check_camera(camera);
+        const gblod_render_params p = check_params(params);
+        if (n) project_points(reinterpret_cast<const float4 *>(d_pts4), d_h, n, *camera, p, d_out, (cudaStream_t)stream);
+    });
+}
+
+} // extern "C"

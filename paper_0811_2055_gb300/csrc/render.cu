@@ -1,0 +1,788 @@
+// Per-frame path: R1 view-dependent node selection (depth paragraph: near nodes deep, far
+// nodes shallow), R2 projection and screen-tile binning, R3 tiled splatting of every point as a
+// blob evaluated at every pixel it covers (GPU paragraph) into 64-bit fixed point, R4 log tone
+// map.  The brute-force frame runs R2-R4 over the raw particle arrays.
+//
+// Determinism: the per-point arithmetic is fp32 with one round-to-nearest per operation in a
+// fixed order, positions are quantised to 1/256 px, the kernel is a 1024-entry integer table
+// and every pixel is an exact 64-bit integer sum, so the image does not depend on launch
+// shape, tiling or the order in which splats are added.
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "lodmath.cuh"
+#include "render.cuh"
+
+namespace gb {
+
+// integer kernel tables (Gaussian, cubic), filled once per device
+__device__ int32_t g_ktab[2][1024];
+
+namespace {
+
+constexpr unsigned ST_RANGE = 1u;
+constexpr int RT = 256;       // render block size
+constexpr int CHUNK = 2048;   // points per block iteration in the projection kernels
+constexpr uint32_t ITEM = 2048; // records per splat work item
+constexpr float A_GAUSS = 0x1.499c68p+29f; // 2^32 / (2 pi (1 - e^-4.5))
+constexpr float A_CUBIC = 0x1.d1a452p+30f; // 2^32 * 10 / (7 pi)
+constexpr float B_GAUSS = 0x1.c71c72p+27f; // 2^31 / 9
+constexpr float B_CUBIC = 0x1p+29f;        // 2^31 / 4
+
+void kernel_table_host(int kernel, int32_t *K)
+{
+    const double qmax = kernel == GBLOD_KERNEL_CUBIC ? 4.0 : 9.0;
+    for (int i = 0; i < 1024; ++i) {
+        const double q = ((double)i + 0.5) * qmax / 1024.0;
+        double f;
+        if (kernel == GBLOD_KERNEL_CUBIC) {
+            const double xi = std::sqrt(q);
+            if (xi < 1.0) {
+                const double a = 1.0 - 1.5 * q;
+                const double b = 0.75 * (q * xi);
+                f = a + b;
+            } else {
+                const double t = 2.0 - xi;
+                f = 0.25 * ((t * t) * t);
+            }
+        } else {
+            f = std::exp(-0.5 * q);
+        }
+        K[i] = (int32_t)std::nearbyint(65536.0 * f);
+    }
+}
+
+void ensure_tables()
+{
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    if ((int)done.size() <= dev) done.resize(dev + 1, 0);
+    if (done[dev]) return;
+    static int32_t K[2][1024];
+    kernel_table_host(GBLOD_KERNEL_GAUSSIAN, K[0]);
+    kernel_table_host(GBLOD_KERNEL_CUBIC, K[1]);
+    GB_CUDA(cudaMemcpyToSymbol(g_ktab, K, sizeof(K)));
+    done[dev] = 1;
+}
+
+struct Proj {
+    float ex, ey, ez, rx, ry, rz, ux, uy, uz, fx, fy, fz;
+    float F, CX, CY, ZN, smin, smax, A, B, Rk, Wf, Hf;
+    int W, H, TW, TH, tiles_x, tiles_y, kernel;
+};
+
+Proj make_proj(const gblod_camera &c, const gblod_render_params &rp)
+{
+    Proj P;
+    P.ex = (float)c.eye[0]; P.ey = (float)c.eye[1]; P.ez = (float)c.eye[2];
+    P.rx = (float)c.right[0]; P.ry = (float)c.right[1]; P.rz = (float)c.right[2];
+    P.ux = (float)c.up[0]; P.uy = (float)c.up[1]; P.uz = (float)c.up[2];
+    P.fx = (float)c.fwd[0]; P.fy = (float)c.fwd[1]; P.fz = (float)c.fwd[2];
+    P.F = (float)c.f_px;
+    P.CX = (float)c.cx;
+    P.CY = (float)c.cy;
+    P.ZN = (float)c.z_near;
+    P.smin = (float)rp.sigma_min_px;
+    P.smax = (float)rp.sigma_max_px;
+    const bool cubic = rp.kernel == GBLOD_KERNEL_CUBIC;
+    P.A = cubic ? A_CUBIC : A_GAUSS;
+    P.B = cubic ? B_CUBIC : B_GAUSS;
+    P.Rk = cubic ? 2.0f : 3.0f;
+    P.Wf = (float)c.width;
+    P.Hf = (float)c.height;
+    P.W = c.width;
+    P.H = c.height;
+    P.TW = rp.tile_w > 0 ? rp.tile_w : 16;
+    P.TH = rp.tile_h > 0 ? rp.tile_h : 16;
+    P.tiles_x = (P.W + P.TW - 1) / P.TW;
+    P.tiles_y = (P.H + P.TH - 1) / P.TH;
+    P.kernel = cubic ? 1 : 0;
+    return P;
+}
+
+struct Splat {
+    int32_t U, V;
+    uint32_t S;
+    float Wf; // amplitude before rounding; Wq = rne(Wf)
+};
+
+// R2 for one point.  Returns 1 drawn, 0 culled, -1 amplitude out of range.
+__device__ __forceinline__ int project(const Proj &P, float x, float y, float z, float w, float h, Splat &s)
+{
+    const float dx = __fsub_rn(x, P.ex), dy = __fsub_rn(y, P.ey), dz = __fsub_rn(z, P.ez);
+    const float xc = __fadd_rn(__fadd_rn(__fmul_rn(P.rx, dx), __fmul_rn(P.ry, dy)), __fmul_rn(P.rz, dz));
+    const float yc = __fadd_rn(__fadd_rn(__fmul_rn(P.ux, dx), __fmul_rn(P.uy, dy)), __fmul_rn(P.uz, dz));
+    const float zc = __fadd_rn(__fadd_rn(__fmul_rn(P.fx, dx), __fmul_rn(P.fy, dy)), __fmul_rn(P.fz, dz));
+    if (!(zc > P.ZN)) return 0;
+    const float iz = __fdiv_rn(1.0f, zc);
+    const float u = __fadd_rn(P.CX, __fmul_rn(__fmul_rn(P.F, xc), iz));
+    const float v = __fsub_rn(P.CY, __fmul_rn(__fmul_rn(P.F, yc), iz));
+    const float sg = __fmul_rn(__fmul_rn(P.F, h), iz);
+    const float sigma = sg >= P.smin ? (sg <= P.smax ? sg : P.smax) : P.smin;
+    const float s2 = __fmul_rn(sigma, sigma);
+    const float Wf = __fdiv_rn(__fmul_rn(w, P.A), s2);
+    const float Sf = __fdiv_rn(P.B, s2);
+    const float R = __fadd_rn(__fmul_rn(P.Rk, sigma), 2.0f);
+    if (!(__fadd_rn(u, R) >= 0.0f && __fsub_rn(u, R) <= P.Wf && __fadd_rn(v, R) >= 0.0f &&
+          __fsub_rn(v, R) <= P.Hf))
+        return 0;
+    if (!(Wf >= 0.0f && Wf < 0x1p48f)) return -1;
+    s.U = __float2int_rn(__fmul_rn(u, 256.0f));
+    s.V = __float2int_rn(__fmul_rn(v, 256.0f));
+    s.S = __float2uint_rn(Sf);
+    s.Wf = Wf;
+    return 1;
+}
+
+// Pixel box (inclusive) that contains every pixel where the table index can be below 1024:
+// q S < 2^47 needs |d| < sqrt(2^47 / S) in 1/256 px.
+__device__ __forceinline__ void splat_box(int U, int V, uint32_t S, int W, int H, int &x0, int &x1, int &y0, int &y1)
+{
+    const float ql = __fdiv_rn(140737488355328.0f, __uint2float_rn(S));
+    const int r = (int)sqrtf(ql) + 2;
+    const int ax = U - 128 - r, bx = U - 128 + r, ay = V - 128 - r, by = V - 128 + r;
+    x0 = -((-ax) >> 8);
+    x1 = bx >> 8;
+    y0 = -((-ay) >> 8);
+    y1 = by >> 8;
+    x0 = max(x0, 0);
+    y0 = max(y0, 0);
+    x1 = min(x1, W - 1);
+    y1 = min(y1, H - 1);
+}
+
+// ------------------------------------------------------------------ R1
+struct Frustum {
+    double n[5][3];
+    double off[5];
+    double E[3];
+    double lo[3];
+    double F, side, lam2, zn2, rk;
+};
+
+Frustum make_frustum(const gblod_camera &c, const gblod_render_params &rp, const gblod_octree *o)
+{
+    // host FP64, every product and sum rounded on its own (built with -ffp-contract=off)
+    Frustum f;
+    const double rk = rp.kernel == GBLOD_KERNEL_CUBIC ? 2.0 : 3.0;
+    const double M = rk * rp.sigma_min_px + 2.0;
+    const double F = c.f_px;
+    const double cl = c.cx + M;
+    const double cr = ((double)c.width + M) - c.cx;
+    const double ct = c.cy + M;
+    const double cb = ((double)c.height + M) - c.cy;
+    for (int a = 0; a < 3; ++a) {
+        f.n[0][a] = c.fwd[a];
+        double t1, t2;
+        t1 = F * c.right[a]; t2 = cl * c.fwd[a]; f.n[1][a] = t1 + t2;
+        t1 = -(F * c.right[a]); t2 = cr * c.fwd[a]; f.n[2][a] = t1 + t2;
+        t1 = -(F * c.up[a]); t2 = ct * c.fwd[a]; f.n[3][a] = t1 + t2;
+        t1 = F * c.up[a]; t2 = cb * c.fwd[a]; f.n[4][a] = t1 + t2;
+        f.E[a] = c.eye[a];
+        f.lo[a] = o->lo[a];
+    }
+    f.off[0] = -c.z_near;
+    f.off[1] = f.off[2] = f.off[3] = f.off[4] = 0.0;
+    f.F = F;
+    f.side = o->side;
+    const double lam = rp.lambda_px < 0.0 ? std::sqrt((double)o->n_max) : rp.lambda_px;
+    f.lam2 = lam * lam;
+    f.zn2 = c.z_near * c.z_near;
+    f.rk = rk;
+    return f;
+}
+
+// 0 cull, 1 emit, 2 refine
+__device__ __forceinline__ int classify(const gblod_node &g, const Frustum &fr)
+{
+    const double rho = __dmul_rn(fr.rk, (double)g.h_cull);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double s = fr.off[k];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double na = fr.n[k][a];
+            const double pa = na > 0.0 ? __dsub_rn(__dadd_rn((double)g.bmax[a], rho), fr.E[a])
+                                       : __dsub_rn(__dsub_rn((double)g.bmin[a], rho), fr.E[a]);
+            s = __dadd_rn(s, __dmul_rn(na, pa));
+        }
+        if (s < 0.0) return 0;
+    }
+    if (!(g.flags & GBLOD_NODE_INTERNAL)) return 1;
+    const int d = g.depth;
+    const uint64_t pfx = g.code ^ (1ull << (3 * d));
+    const uint32_t q[3] = {gbd::compact3(pfx >> 2), gbd::compact3(pfx >> 1), gbd::compact3(pfx)};
+    const double e = ldexp(fr.side, -d);
+    double d2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double blo = __dadd_rn(fr.lo[a], __dmul_rn(e, (double)q[a]));
+        const double bhi = __dadd_rn(blo, e);
+        const double E = fr.E[a];
+        const double da = E < blo ? __dsub_rn(blo, E) : (E > bhi ? __dsub_rn(E, bhi) : 0.0);
+        d2 = __dadd_rn(d2, __dmul_rn(da, da));
+    }
+    const double fe = __dmul_rn(fr.F, e);
+    const double lhs = __dmul_rn(fe, fe);
+    const double rhs = __dmul_rn(fr.lam2, d2 > fr.zn2 ? d2 : fr.zn2);
+    return lhs > rhs ? 2 : 1;
+}
+
+__global__ void k_select_init(uint32_t *front, uint32_t *cnt)
+{
+    front[0] = 0u;
+    cnt[0] = 1u;
+}
+
+__global__ void __launch_bounds__(RT) k_select_level(const gblod_node *__restrict__ nodes, Frustum fr,
+                                                     const uint32_t *__restrict__ fin, const uint32_t *nin,
+                                                     uint32_t *__restrict__ fout, uint32_t *nout,
+                                                     uint32_t *__restrict__ sel, uint32_t *nsel)
+{
+    const uint32_t n = *nin;
+    const uint32_t lt = gbd::lanemask_lt();
+    const int lane = threadIdx.x & 31;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        int cls = 0;
+        uint32_t node = 0, ccount = 0, cfirst = 0;
+        if (i < n) {
+            node = fin[i];
+            const gblod_node g = nodes[node];
+            cls = classify(g, fr);
+            ccount = g.child_count;
+            cfirst = g.child_first;
+        }
+        // warp-aggregated appends
+        const uint32_t em = __ballot_sync(0xffffffffu, cls == 1);
+        if (em) {
+            const int leader = __ffs(em) - 1;
+            uint32_t b = 0;
+            if (lane == leader) b = atomicAdd(nsel, (uint32_t)__popc(em));
+            b = __shfl_sync(0xffffffffu, b, leader);
+            if (cls == 1) sel[b + __popc(em & lt)] = node;
+        }
+        uint32_t want = cls == 2 ? ccount : 0u, incl = want;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+            uint32_t b = 0;
+            if (lane == 31) b = atomicAdd(nout, total);
+            b = __shfl_sync(0xffffffffu, b, 31);
+            const uint32_t at = b + incl - want;
+            for (uint32_t k = 0; k < want; ++k) fout[at + k] = cfirst + k;
+        }
+    }
+}
+
+// exclusive prefix of the selected nodes' point counts; base[j] maps a flat index to a point
+__global__ void __launch_bounds__(1024) k_sel_prefix(const gblod_node *__restrict__ nodes,
+                                                     const uint32_t *__restrict__ sel, const uint32_t *nsel,
+                                                     uint64_t *__restrict__ pfx, int64_t *__restrict__ base,
+                                                     FrameStatsDev *stats)
+{
+    __shared__ unsigned long long wsum[32];
+    const uint32_t n = *nsel;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long run = 0;
+    for (uint32_t start = 0; start < n; start += 1024) {
+        const uint32_t i = start + threadIdx.x;
+        unsigned long long c = 0, pf = 0;
+        if (i < n) {
+            const gblod_node &g = nodes[sel[i]];
+            c = g.point_count;
+            pf = g.point_first;
+        }
+        unsigned long long incl = c;
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        unsigned long long before = 0, all = 0;
+        for (int w = 0; w < 32; ++w) {
+            before += w < warp ? wsum[w] : 0ull;
+            all += wsum[w];
+        }
+        const unsigned long long ex = run + before + incl - c;
+        if (i < n) {
+            pfx[i] = ex;
+            base[i] = (int64_t)pf - (int64_t)ex;
+        }
+        run += all;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pfx[n] = run;
+        stats->points = run;
+        stats->nodes_selected = n;
+    }
+}
+
+// ------------------------------------------------------------------ R2
+struct SrcLOD {
+    const float4 *pts4;
+    const float *hs;
+    const uint64_t *pfx;  // n_sel + 1 entries
+    const int64_t *base;
+    const uint32_t *nsel;
+    const unsigned long long *total;
+};
+
+struct SrcFlat {
+    const float *xyz, *mass, *h;
+    unsigned long long n;
+};
+
+__device__ __forceinline__ unsigned long long src_total(const SrcLOD &s) { return *s.total; }
+__device__ __forceinline__ unsigned long long src_total(const SrcFlat &s) { return s.n; }
+
+// per block iteration: locate the selected nodes covering [a, b)
+__device__ __forceinline__ void src_range(const SrcLOD &s, unsigned long long a, unsigned long long b, uint32_t &j0,
+                                          uint32_t &j1)
+{
+    __shared__ uint32_t sj[2];
+    if (threadIdx.x < 2) {
+        const unsigned long long v = threadIdx.x == 0 ? a : b - 1;
+        uint32_t lo = 0, hi = *s.nsel; // largest j with pfx[j] <= v
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s.pfx[mid] <= v)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        sj[threadIdx.x] = lo;
+    }
+    __syncthreads();
+    j0 = sj[0];
+    j1 = sj[1];
+    __syncthreads();
+}
+__device__ __forceinline__ void src_range(const SrcFlat &, unsigned long long, unsigned long long, uint32_t &j0,
+                                          uint32_t &j1)
+{
+    j0 = j1 = 0;
+}
+
+__device__ __forceinline__ void src_load(const SrcLOD &s, unsigned long long e, uint32_t j0, uint32_t j1, float &x,
+                                         float &y, float &z, float &w, float &h)
+{
+    uint32_t lo = j0, hi = j1 + 1;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s.pfx[mid] <= e)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const unsigned long long p = (unsigned long long)((long long)e + s.base[lo]);
+    const float4 q = s.pts4[p];
+    x = q.x; y = q.y; z = q.z; w = q.w;
+    h = s.hs[p];
+}
+__device__ __forceinline__ void src_load(const SrcFlat &s, unsigned long long e, uint32_t, uint32_t, float &x,
+                                         float &y, float &z, float &w, float &h)
+{
+    x = s.xyz[3 * e];
+    y = s.xyz[3 * e + 1];
+    z = s.xyz[3 * e + 2];
+    w = s.mass[e];
+    h = s.h[e];
+}
+
+template <class Src>
+__global__ void __launch_bounds__(RT) k_project_count(Src src, Proj P, uint32_t *__restrict__ tile_cnt,
+                                                      unsigned *status, FrameStatsDev *stats)
+{
+    const unsigned long long total = src_total(src);
+    const int lane = threadIdx.x & 31;
+    unsigned long long splats = 0;
+    for (unsigned long long a = (unsigned long long)blockIdx.x * CHUNK; a < total;
+         a += (unsigned long long)gridDim.x * CHUNK) {
+        const unsigned long long b = min(total, a + CHUNK);
+        uint32_t j0, j1;
+        src_range(src, a, b, j0, j1);
+        for (unsigned long long e0 = a; e0 < b; e0 += RT) {
+            const unsigned long long e = e0 + threadIdx.x;
+            int res = 0;
+            Splat s;
+            if (e < b) {
+                float x, y, z, w, h;
+                src_load(src, e, j0, j1, x, y, z, w, h);
+                res = project(P, x, y, z, w, h, s);
+            }
+            if (__any_sync(0xffffffffu, res < 0) && lane == 0) atomicOr(status, ST_RANGE);
+            unsigned long long wq = res == 1 ? __float2ull_rn(s.Wf) : 0ull;
+            for (int d = 16; d > 0; d >>= 1) wq += __shfl_xor_sync(0xffffffffu, wq, d);
+            if (lane == 0 && wq) {
+                const unsigned long long old = atomicAdd(&stats->amp_lo, wq);
+                if (old + wq < old) atomicAdd(&stats->amp_hi, 1ull);
+            }
+            if (res == 1) {
+                ++splats;
+                int x0, x1, y0, y1;
+                splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
+                if (x0 <= x1 && y0 <= y1) {
+                    const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
+                    for (int ty = ty0; ty <= ty1; ++ty)
+                        for (int tx = tx0; tx <= tx1; ++tx) {
+                            const uint32_t t = (uint32_t)(ty * P.tiles_x + tx);
+                            const uint32_t mask = __activemask();
+                            const uint32_t peers = __match_any_sync(mask, t);
+                            const int leader = __ffs(peers) - 1;
+                            if (lane == leader) atomicAdd(&tile_cnt[t], (uint32_t)__popc(peers));
+                        }
+                }
+            }
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) splats += __shfl_xor_sync(0xffffffffu, splats, d);
+    if (lane == 0 && splats) atomicAdd(&stats->splats, splats);
+}
+
+template <class Src>
+__global__ void __launch_bounds__(RT) k_project_scatter(Src src, Proj P, uint32_t *__restrict__ cursor,
+                                                        uint4 *__restrict__ rec)
+{
+    const unsigned long long total = src_total(src);
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = gbd::lanemask_lt();
+    for (unsigned long long a = (unsigned long long)blockIdx.x * CHUNK; a < total;
+         a += (unsigned long long)gridDim.x * CHUNK) {
+        const unsigned long long b = min(total, a + CHUNK);
+        uint32_t j0, j1;
+        src_range(src, a, b, j0, j1);
+        for (unsigned long long e0 = a; e0 < b; e0 += RT) {
+            const unsigned long long e = e0 + threadIdx.x;
+            int res = 0;
+            Splat s;
+            if (e < b) {
+                float x, y, z, w, h;
+                src_load(src, e, j0, j1, x, y, z, w, h);
+                res = project(P, x, y, z, w, h, s);
+            }
+            if (res == 1) {
+                int x0, x1, y0, y1;
+                splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
+                if (x0 <= x1 && y0 <= y1) {
+                    const uint4 r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
+                    const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
+                    for (int ty = ty0; ty <= ty1; ++ty)
+                        for (int tx = tx0; tx <= tx1; ++tx) {
+                            const uint32_t t = (uint32_t)(ty * P.tiles_x + tx);
+                            const uint32_t mask = __activemask();
+                            const uint32_t peers = __match_any_sync(mask, t);
+                            const int leader = __ffs(peers) - 1;
+                            uint32_t base = 0;
+                            if (lane == leader) base = atomicAdd(&cursor[t], (uint32_t)__popc(peers));
+                            base = __shfl_sync(peers, base, leader);
+                            rec[base + __popc(peers & lt)] = r;
+                        }
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_tile_items(uint32_t ntiles, const uint32_t *tile_cnt, uint32_t *item_cnt)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles) item_cnt[t] = (tile_cnt[t] + ITEM - 1) / ITEM;
+}
+
+__global__ void k_fill_items(uint32_t ntiles, const uint32_t *tile_cnt, const uint32_t *tile_off,
+                             const uint32_t *item_off, uint4 *items)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const uint32_t c = tile_cnt[t], o = tile_off[t];
+    uint32_t k = item_off[t];
+    for (uint32_t s = 0; s < c; s += ITEM, ++k) items[k] = make_uint4(t, o + s, o + min(c, s + ITEM), 0u);
+}
+
+// ------------------------------------------------------------------ R3
+__global__ void __launch_bounds__(RT) k_splat_tiles(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
+                                                    Proj P, unsigned long long *__restrict__ img)
+{
+    extern __shared__ unsigned long long acc[]; // TW * TH
+    __shared__ int32_t K[1024];
+    const int npix = P.TW * P.TH;
+    for (int i = threadIdx.x; i < 1024; i += RT) K[i] = g_ktab[P.kernel][i];
+    for (int i = threadIdx.x; i < npix; i += RT) acc[i] = 0ull;
+    __syncthreads();
+    const uint4 it = items[blockIdx.x];
+    const int tx = (int)(it.x % (uint32_t)P.tiles_x), ty = (int)(it.x / (uint32_t)P.tiles_x);
+    const int X0 = tx * P.TW, Y0 = ty * P.TH;
+    const int X1 = min(X0 + P.TW, P.W) - 1, Y1 = min(Y0 + P.TH, P.H) - 1;
+    for (uint32_t r = it.y + threadIdx.x; r < it.z; r += RT) {
+        const uint4 R = rec[r];
+        const int U = (int)R.x, V = (int)R.y;
+        const uint32_t S = R.z;
+        const unsigned long long Wq = __float2ull_rn(__uint_as_float(R.w));
+        int x0, x1, y0, y1;
+        splat_box(U, V, S, P.W, P.H, x0, x1, y0, y1);
+        x0 = max(x0, X0);
+        x1 = min(x1, X1);
+        y0 = max(y0, Y0);
+        y1 = min(y1, Y1);
+        for (int py = y0; py <= y1; ++py) {
+            const int dy = py * 256 + 128 - V;
+            const long long dy2 = (long long)dy * dy;
+            for (int px = x0; px <= x1; ++px) {
+                const int dx = px * 256 + 128 - U;
+                const unsigned long long q = (unsigned long long)((long long)dx * dx + dy2);
+                const unsigned long long t = (q * (unsigned long long)S) >> 37;
+                if (t < 1024ull) {
+                    const unsigned long long c = (Wq * (unsigned long long)(uint32_t)K[t]) >> 16;
+                    atomicAdd(&acc[(py - Y0) * P.TW + (px - X0)], c);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < npix; i += RT) {
+        const unsigned long long v = acc[i];
+        const int gx = X0 + i % P.TW, gy = Y0 + i / P.TW;
+        if (v && gx < P.W && gy < P.H) atomicAdd(&img[(size_t)gy * P.W + gx], v);
+    }
+}
+
+// ------------------------------------------------------------------ R4
+__global__ void k_image_max(const unsigned long long *img, size_t n, unsigned long long *out)
+{
+    unsigned long long m = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = img[i] > m ? img[i] : m;
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, d);
+        m = o > m ? o : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// out = 0 if I <= lo, else min(255, rne(255 ln(I/lo) / ln(hi/lo))), I = acc 2^-32
+__global__ void k_tonemap(const unsigned long long *img, size_t n, const unsigned long long *maxv, int auto_range,
+                          double lo_acc_fixed, double hi_acc_fixed, uint8_t *out)
+{
+    __shared__ double s_lo;
+    __shared__ float s_l2lo, s_scale;
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        double hi = hi_acc_fixed, lo = lo_acc_fixed;
+        if (auto_range) {
+            hi = (double)*maxv;
+            lo = hi * 1e-4;
+        }
+        s_ok = (hi > 0.0 && lo > 0.0 && hi > lo) ? 1 : 0;
+        s_lo = lo;
+        s_l2lo = s_ok ? (float)log2(lo) : 0.0f;
+        s_scale = s_ok ? (float)(255.0 / log2(hi / lo)) : 0.0f;
+    }
+    __syncthreads();
+    const double lo = s_lo;
+    const float l2lo = s_l2lo, scale = s_scale;
+    const int ok = s_ok;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long a = img[i];
+        uint8_t o = 0;
+        if (ok && (double)a > lo) {
+            const float t = rintf((log2f((float)a) - l2lo) * scale);
+            o = (uint8_t)(t > 255.0f ? 255.0f : (t < 0.0f ? 0.0f : t));
+        }
+        out[i] = o;
+    }
+}
+
+__global__ void k_project_debug(const float4 *pts4, const float *h, size_t n, Proj P, long long *out)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float4 q = pts4[i];
+        Splat s;
+        const int r = project(P, q.x, q.y, q.z, q.w, h[i], s);
+        out[5 * i + 0] = r;
+        out[5 * i + 1] = r == 1 ? s.U : 0;
+        out[5 * i + 2] = r == 1 ? s.V : 0;
+        out[5 * i + 3] = r == 1 ? (long long)s.S : 0;
+        out[5 * i + 4] = r == 1 ? (long long)__float2ull_rn(s.Wf) : 0;
+    }
+}
+
+__global__ void k_morton_plain(const float *xyz, size_t n, double lx, double ly, double lz, double scale,
+                               uint64_t *keys)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        keys[i] = gbd::morton_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lx, ly, lz, scale);
+}
+
+// ------------------------------------------------------------------ frame driver
+template <class Src>
+void frame_common(gblod_renderer *r, const Src &src, const Proj &P, const gblod_render_params &rp, uint8_t *image,
+                  uint64_t *accum, cudaStream_t s)
+{
+    const Allocator &A = r->A;
+    const uint32_t ntiles = (uint32_t)(P.tiles_x * P.tiles_y);
+    r->tile_cnt.ensure(A, ntiles, s);
+    r->tile_off.ensure(A, ntiles + 1, s);
+    r->tile_cur.ensure(A, ntiles, s);
+    r->item_cnt.ensure(A, ntiles, s);
+    r->item_off.ensure(A, ntiles + 1, s);
+    GB_CUDA(cudaMemsetAsync(r->tile_cnt.p, 0, (size_t)ntiles * 4, s));
+    const unsigned G = (unsigned)persistent_blocks(4);
+    launch(GBLOD_K_PROJECT_COUNT, k_project_count<Src>, dim3(G), dim3(RT), 0, s, src, P, r->tile_cnt.p, r->status,
+           r->stats);
+    scan_exclusive_u32(A, r->scan, r->tile_cnt.p, r->tile_off.p, ntiles, r->tile_off.p + ntiles, s);
+    launch(GBLOD_K_RENDER_OTHER, k_tile_items, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
+           (const uint32_t *)r->tile_cnt.p, r->item_cnt.p);
+    scan_exclusive_u32(A, r->scan, r->item_cnt.p, r->item_off.p, ntiles, r->item_off.p + ntiles, s);
+    // one read-back per frame: the number of (tile, splat) records and work items
+    uint32_t *h = static_cast<uint32_t *>(r->hs.get(16));
+    GB_CUDA(cudaMemcpyAsync(h, r->tile_off.p + ntiles, 4, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(h + 1, r->item_off.p + ntiles, 4, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    const uint32_t pairs = h[0], nitems = h[1];
+    const unsigned long long pt[2] = {pairs, ntiles};
+    GB_CUDA(cudaMemcpyAsync(&r->stats->pairs, pt, sizeof(pt), cudaMemcpyHostToDevice, s));
+    r->records.ensure(A, pairs, s);
+    r->items.ensure(A, nitems, s);
+    GB_CUDA(cudaMemcpyAsync(r->tile_cur.p, r->tile_off.p, (size_t)ntiles * 4, cudaMemcpyDeviceToDevice, s));
+    launch(GBLOD_K_PROJECT_SCATTER, k_project_scatter<Src>, dim3(G), dim3(RT), 0, s, src, P, r->tile_cur.p,
+           r->records.p);
+    launch(GBLOD_K_RENDER_OTHER, k_fill_items, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
+           (const uint32_t *)r->tile_cnt.p, (const uint32_t *)r->tile_off.p, (const uint32_t *)r->item_off.p,
+           r->items.p);
+    const size_t npix = (size_t)P.W * P.H;
+    unsigned long long *img = reinterpret_cast<unsigned long long *>(accum);
+    if (!img) {
+        r->accum.ensure(A, npix, s);
+        img = r->accum.p;
+    }
+    GB_CUDA(cudaMemsetAsync(img, 0, npix * 8, s));
+    const size_t smem = (size_t)P.TW * P.TH * 8;
+    launch(GBLOD_K_SPLAT, k_splat_tiles, dim3(nitems), dim3(RT), smem, s, (const uint4 *)r->records.p,
+           (const uint4 *)r->items.p, P, img);
+    if (image) {
+        r->maxv.ensure(A, 1, s);
+        double lo = 0.0, hi = 0.0;
+        if (rp.tone_auto) {
+            GB_CUDA(cudaMemsetAsync(r->maxv.p, 0, 8, s));
+            launch(GBLOD_K_TONEMAP, k_image_max, dim3(persistent_blocks(2)), dim3(256), 0, s,
+                   (const unsigned long long *)img, npix, r->maxv.p);
+        } else {
+            lo = std::ldexp(rp.tone_lo, 32);
+            hi = std::ldexp(rp.tone_hi, 32);
+        }
+        launch(GBLOD_K_TONEMAP, k_tonemap, dim3(persistent_blocks(2)), dim3(256), 0, s,
+               (const unsigned long long *)img, npix, (const unsigned long long *)r->maxv.p, rp.tone_auto ? 1 : 0,
+               lo, hi, image);
+    }
+}
+
+} // namespace
+
+void renderer_init(gblod_renderer *r, cudaStream_t s)
+{
+    ensure_tables();
+    r->status = static_cast<unsigned *>(r->A.get(sizeof(unsigned), s));
+    r->stats = static_cast<FrameStatsDev *>(r->A.get(sizeof(FrameStatsDev), s));
+    GB_CUDA(cudaMemsetAsync(r->status, 0, sizeof(unsigned), s));
+    GB_CUDA(cudaMemsetAsync(r->stats, 0, sizeof(FrameStatsDev), s));
+    GB_CUDA(cudaStreamSynchronize(s));
+}
+
+void renderer_release(gblod_renderer *r)
+{
+    cudaStream_t s = r->last_stream;
+    const Allocator &A = r->A;
+    if (s) (void)cudaStreamSynchronize(s);
+    A.put(r->status, sizeof(unsigned), s);
+    A.put(r->stats, sizeof(FrameStatsDev), s);
+    r->frontA.release(A, s); r->frontB.release(A, s); r->sel.release(A, s); r->lvl_cnt.release(A, s);
+    r->sel_pfx.release(A, s); r->sel_base.release(A, s);
+    r->tile_cnt.release(A, s); r->tile_off.release(A, s); r->tile_cur.release(A, s);
+    r->item_cnt.release(A, s); r->item_off.release(A, s);
+    r->records.release(A, s); r->items.release(A, s); r->accum.release(A, s); r->maxv.release(A, s);
+    r->scan.buf.release(A, s);
+}
+
+static void check_image(const gblod_camera &c)
+{
+    if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384)
+        fail(GBLOD_ERR_INVALID_ARG, "camera width/height must be in 1..16384");
+}
+
+void render_lod(gblod_renderer *r, const gblod_octree *o, const gblod_camera &cam, const gblod_render_params &rp,
+                uint8_t *image, uint64_t *accum, cudaStream_t s)
+{
+    check_image(cam);
+    r->last_stream = s;
+    r->last_was_lod = true;
+    const Allocator &A = r->A;
+    const Proj P = make_proj(cam, rp);
+    GB_CUDA(cudaMemsetAsync(r->stats, 0, sizeof(FrameStatsDev), s));
+    const uint64_t nn = o->n_nodes;
+    const int levels = o->depth_max + 1;
+    r->frontA.ensure(A, nn + 1, s);
+    r->frontB.ensure(A, nn + 1, s);
+    r->sel.ensure(A, nn + 1, s);
+    r->lvl_cnt.ensure(A, levels + 2, s);
+    r->sel_pfx.ensure(A, nn + 2, s);
+    r->sel_base.ensure(A, nn + 1, s);
+    GB_CUDA(cudaMemsetAsync(r->lvl_cnt.p, 0, (size_t)(levels + 2) * 4, s));
+    uint32_t *nsel = r->lvl_cnt.p + levels + 1;
+    if (nn > 0) {
+        const Frustum fr = make_frustum(cam, rp, o);
+        launch(GBLOD_K_SELECT_NODES, k_select_init, dim3(1), dim3(1), 0, s, r->frontA.p, r->lvl_cnt.p);
+        uint32_t *fin = r->frontA.p, *fout = r->frontB.p;
+        const unsigned G = (unsigned)persistent_blocks(2);
+        for (int d = 0; d < levels; ++d) {
+            launch(GBLOD_K_SELECT_NODES, k_select_level, dim3(G), dim3(RT), 0, s, (const gblod_node *)o->nodes, fr,
+                   (const uint32_t *)fin, (const uint32_t *)(r->lvl_cnt.p + d), fout, r->lvl_cnt.p + d + 1,
+                   r->sel.p, nsel);
+            std::swap(fin, fout);
+        }
+    }
+    launch(GBLOD_K_SELECT_NODES, k_sel_prefix, dim3(1), dim3(1024), 0, s, (const gblod_node *)o->nodes,
+           (const uint32_t *)r->sel.p, (const uint32_t *)nsel, r->sel_pfx.p, r->sel_base.p, r->stats);
+    SrcLOD src{o->pts4, o->hs, r->sel_pfx.p, r->sel_base.p, nsel, &r->stats->points};
+    frame_common(r, src, P, rp, image, accum, s);
+}
+
+void render_brute(gblod_renderer *r, const float *xyz, const float *mass, const float *h, uint64_t n,
+                  const gblod_camera &cam, const gblod_render_params &rp, uint8_t *image, uint64_t *accum,
+                  cudaStream_t s)
+{
+    check_image(cam);
+    r->last_stream = s;
+    r->last_was_lod = false;
+    const Proj P = make_proj(cam, rp);
+    GB_CUDA(cudaMemsetAsync(r->stats, 0, sizeof(FrameStatsDev), s));
+    const unsigned long long pts[1] = {n};
+    GB_CUDA(cudaMemcpyAsync(&r->stats->points, pts, 8, cudaMemcpyHostToDevice, s));
+    SrcFlat src{xyz, mass, h, n};
+    frame_common(r, src, P, rp, image, accum, s);
+}
+
+void project_points(const float4 *pts4, const float *h, uint64_t n, const gblod_camera &cam,
+                    const gblod_render_params &rp, int64_t *out, cudaStream_t s)
+{
+    const Proj P = make_proj(cam, rp);
+    launch(GBLOD_K_RENDER_OTHER, k_project_debug, dim3(persistent_blocks(4)), dim3(256), 0, s, pts4, h, (size_t)n, P,
+           reinterpret_cast<long long *>(out));
+}
+
+void morton_keys(const float *xyz, uint64_t n, const double lo[3], double side, uint64_t *keys, cudaStream_t s)
+{
+    launch(GBLOD_K_MORTON, k_morton_plain, dim3(persistent_blocks(4)), dim3(256), 0, s, xyz, (size_t)n, lo[0], lo[1],
+           lo[2], 2097152.0 / side, keys);
+}
+
+} // namespace gb

@@ -1,0 +1,41 @@
+// Render workspace and the frame entry points shared by the C ABI.
+#pragma once
+
+#include "octree.cuh"
+
+namespace gb {
+struct FrameStatsDev {
+    unsigned long long nodes_selected, points, splats, pairs, tiles, amp_lo, amp_hi, items;
+};
+} // namespace gb
+
+struct gblod_renderer {
+    gb::Allocator A;
+    gb::HostStage hs;
+    gb::ScanTmp scan;
+    unsigned *status = nullptr;             // sticky device status bits
+    gb::FrameStatsDev *stats = nullptr;     // device counters of the last frame
+    // R1
+    gb::DBuf<uint32_t> frontA, frontB, sel, lvl_cnt;
+    gb::DBuf<uint64_t> sel_pfx;
+    gb::DBuf<int64_t> sel_base;
+    // R2 / R3
+    gb::DBuf<uint32_t> tile_cnt, tile_off, tile_cur, item_cnt, item_off;
+    gb::DBuf<uint4> records, items;
+    gb::DBuf<unsigned long long> accum, maxv;
+    cudaStream_t last_stream = nullptr;
+    bool last_was_lod = false;
+};
+
+namespace gb {
+void renderer_init(gblod_renderer *r, cudaStream_t s);
+void renderer_release(gblod_renderer *r);
+void render_lod(gblod_renderer *r, const gblod_octree *o, const gblod_camera &cam, const gblod_render_params &rp,
+                uint8_t *image, uint64_t *accum, cudaStream_t s);
+void render_brute(gblod_renderer *r, const float *xyz, const float *mass, const float *h, uint64_t n,
+                  const gblod_camera &cam, const gblod_render_params &rp, uint8_t *image, uint64_t *accum,
+                  cudaStream_t s);
+void project_points(const float4 *pts4, const float *h, uint64_t n, const gblod_camera &cam,
+                    const gblod_render_params &rp, int64_t *out, cudaStream_t s);
+void morton_keys(const float *xyz, uint64_t n, const double lo[3], double side, uint64_t *keys, cudaStream_t s);
+} // namespace gb

@@ -1,0 +1,39 @@
+"""Shared helpers of the GPU parity tests (inputs go to both sides from the same arrays)."""
+import numpy as np
+import torch
+
+from oracle import oracle as O
+
+NODE_FIELDS = ("code", "seg_first", "point_first", "mass_lo", "mass_hi", "seg_count", "point_count", "child_first",
+               "child_count", "depth", "flags", "parent", "h_cull", "w_rep", "s_rep", "bmin", "bmax")
+
+
+def dev():
+    return torch.device("cuda", 0)
+
+
+def to_dev(*arrays):
+    return tuple(torch.from_numpy(np.ascontiguousarray(a)).to(dev()) for a in arrays)
+
+
+def compare_trees(ex: dict, ot: "O.OracleTree"):
+    """Bit-exact comparison of a GPU octree export with the oracle's tree."""
+    gn, on = ex["nodes"], ot.nodes
+    assert len(gn) == len(on), (len(gn), len(on))
+    for f in NODE_FIELDS:
+        a, b = gn[f], on[f]
+        if not np.array_equal(a, b):
+            bad = np.nonzero(a != b)[0][:5]
+            raise AssertionError(f"node field {f} differs at {bad}: gpu {a[bad]} oracle {b[bad]}")
+    assert ex["depth_max"] == ot.depth_max
+    assert ex["equal_mass"] == ot.equal_mass
+    assert np.array_equal(ex["skey"], ot.skey), "sorted keys differ"
+    assert np.array_equal(ex["sidx"], ot.sidx), "sort permutation differs"
+    assert np.array_equal(ex["pt_src"], ot.pt_src), "representative choice differs"
+    assert np.array_equal(ex["pts4"].view(np.uint32), ot.pts4.view(np.uint32)), "stored points differ"
+    assert np.array_equal(ex["hs"].view(np.uint32), ot.hs.view(np.uint32)), "stored smoothing lengths differ"
+
+
+def u8_close(a, b, tol=1):
+    d = np.abs(np.asarray(a).astype(np.int32) - np.asarray(b).astype(np.int32))
+    return int(d.max()) if d.size else 0
