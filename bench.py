@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 level-of-detail renderer (one JSON line on stdout, rank 0).
+
+Workload (default `mid`): 2^24 synthetic particles in 4096 NFW halos + 10% background, octree
+with n_max = 16000, and the 240-frame 1920x1080 helical fly-through.  One step = one pass of the
+whole hot path: build the octree on the device (A1-A5), then render all 240 frames at level of
+detail (R1-R4).  `value` is LOD frames/s over the timed steps (build included).  The same frames
+rendered from every particle (brute force) are timed separately under "all_points".
+
+--impl reference times the CPU oracle (test infrastructure, plain C) on the host cores instead.
+Multi-GPU (torchrun): every rank runs the full step on its own replica (weak scaling, no
+collective on the data path); value = frames of all ranks / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "splats/s & 1080p frames/s (LOD vs all points); p50/p99 frame latency"
+OPS_PER_PIXEL_UPDATE = 12  # integer ops of one (splat, pixel) contribution, see the design doc
+SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["mid", "paper", "tiny"], default="mid")
+    ap.add_argument("--frames", type=int, default=0, help="frames per step (0 = the workload's path)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-brute", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name: str, frames: int):
+    from paper_0811_2055_gb300 import synth
+    if name == "mid":
+        p = synth.mid()
+        nf = frames or 240
+        cams = [synth.helix_view(k * 240 // nf) for k in range(nf)]
+        desc = ("mid: 2^24 particles (4096 NFW halos, dN/dM ~ M^-1.9, c in [5,15], + 10% uniform), n_max 16000, "
+                f"{nf}-frame 1920x1080 helical fly-through")
+    elif name == "paper":
+        p = synth.paper_scale()
+        nf = frames or 8
+        cams = [synth.paper_view(j % 8) for j in range(nf)]
+        desc = ("paper: 150M particles (65,536 NFW halos + central halo with 30% + 10% uniform), n_max 16000, "
+                "8 views at 1920x1080 from inside the central halo out to the whole box")
+    else:
+        p = synth.tiny()
+        nf = frames or 1
+        cams = [synth.tiny_view()] * nf
+        desc = "tiny: 262,144 particles (64 Plummer spheres + 20% uniform), n_max 16000, 512x512 view"
+    return p, cams, 16000, desc
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        sel = str(gpu)
+        try:
+            import torch
+            u = getattr(torch.cuda.get_device_properties(gpu), "uuid", None)
+            if u is not None:
+                sel = "GPU-" + str(u) if not str(u).startswith("GPU-") else str(u)
+        except Exception:
+            pass
+        self.gpu = sel
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", sel, f"--query-gpu={self.Q}", "--format=csv,noheader",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        rows = []
+        for ln in open(self.f.name):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1].split()[0]), float(parts[2].split()[0]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows), "reasons": seen,
+                "samples": len(rows)}
+
+
+def dist_info():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ------------------------------------------------------------------ our implementation
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_0811_2055_gb300 import gblod
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    p, cams, n_max, desc = workload(a.workload, a.frames)
+    W, H = cams[0]["width"], cams[0]["height"]
+    xyz, mass, h = (torch.from_numpy(x).to(dev) for x in (p.xyz, p.mass, p.h))
+    r = gblod.Renderer()
+    lam = math.sqrt(n_max)
+    par = gblod.make_params(lambda_px=lam)
+    img = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    acc = torch.empty((H, W), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    nf = len(cams)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def lod_step(ev=None):
+        if ev is not None:
+            ev[0].record()
+        tree = gblod.build_lod(xyz, mass, h, n_max=n_max, seed=1)
+        if ev is not None:
+            ev[1].record()
+        for k, cam in enumerate(cams):
+            if ev is not None:
+                ev[2 + 2 * k].record()
+            r.render(tree, cam, par, image=img, accum=acc)
+            if ev is not None:
+                ev[3 + 2 * k].record()
+        return tree
+
+    def brute_step(ev=None):
+        for k, cam in enumerate(cams):
+            if ev is not None:
+                ev[2 * k].record()
+            r.render_bruteforce(xyz, mass, h, cam, par, image=img, accum=acc)
+            if ev is not None:
+                ev[2 * k + 1].record()
+
+    def timed(fn, n_ev, steps, warm, probe=None):
+        for _ in range(warm):
+            out = fn()
+            if out is not None:
+                out.free()
+        torch.cuda.synchronize()
+        tot_ms, frame_ms, build_ms = 0.0, [], []
+        l0 = gblod.launch_count()
+        if probe is not None:
+            gblod.probe_enable(probe)
+        for _ in range(steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            barrier()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = fn(ev)
+            e1.record()
+            torch.cuda.synchronize()
+            barrier()
+            tot_ms += e0.elapsed_time(e1)
+            if out is not None:  # LOD step: build events first
+                build_ms.append(ev[0].elapsed_time(ev[1]))
+                frame_ms += [ev[2 + 2 * k].elapsed_time(ev[3 + 2 * k]) for k in range(nf)]
+                out.free()
+            else:
+                frame_ms += [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(nf)]
+        launches = gblod.launch_count() - l0
+        pr = gblod.probe_read() if probe is not None else None
+        if probe is not None:
+            gblod.probe_enable(gblod.K_ANY)
+        return tot_ms, frame_ms, build_ms, launches, pr
+
+    # census of one LOD pass and one brute pass (untimed; the counts are deterministic)
+    tree = lod_step()
+    lod_counts = {"splats": 0, "points": 0, "pixel_updates": 0, "nodes": 0}
+    for cam in cams:
+        r.render(tree, cam, par, image=img, accum=acc)
+        s = r.stats()
+        lod_counts["splats"] += s["splats"]
+        lod_counts["points"] += s["points"]
+        lod_counts["pixel_updates"] += s["pixel_updates"]
+        lod_counts["nodes"] += s["nodes_selected"]
+    info = tree.info()
+    tree.free()
+    assert r.status() == gblod.OK
+
+    clocks = Clocks(local)
+    upd0 = r.stats()["pixel_updates_total"]
+    tot_ms, frame_ms, build_ms, launches, pr = timed(lod_step, 2 + 2 * nf, a.steps, a.warmup, probe=gblod.K_SPLAT)
+    upd = r.stats()["pixel_updates_total"] - upd0
+    ck = clocks.stop()
+
+    brute = None
+    if not a.no_brute:
+        b_counts = {"splats": 0, "pixel_updates": 0}
+        for cam in cams:
+            r.render_bruteforce(xyz, mass, h, cam, par, image=img, accum=acc)
+            s = r.stats()
+            b_counts["splats"] += s["splats"]
+            b_counts["pixel_updates"] += s["pixel_updates"]
+        b_ms, b_frames, _, _, _ = timed(brute_step, 2 * nf, a.steps, a.warmup)
+        brute = dict(frames_per_s=a.steps * nf / (b_ms / 1e3), ms_per_frame=b_ms / (a.steps * nf),
+                     splats_per_s=a.steps * b_counts["splats"] / (b_ms / 1e3),
+                     points_per_s=a.steps * nf * p.n / (b_ms / 1e3),
+                     p50_ms=float(np.percentile(b_frames, 50)), p99_ms=float(np.percentile(b_frames, 99)),
+                     splats_per_frame=b_counts["splats"] / nf, pixel_updates_per_frame=b_counts["pixel_updates"] / nf)
+
+    # end to end through the public API: pinned host inputs in, u8 frames out, every step
+    e2e = None
+    if not a.no_e2e:
+        hx, hm, hh = (torch.from_numpy(x).pin_memory() for x in (p.xyz, p.mass, p.h))
+        out_h = torch.empty((H, W), dtype=torch.uint8).pin_memory()
+        dx, dm, dh = torch.empty_like(xyz), torch.empty_like(mass), torch.empty_like(h)
+
+        def e2e_step():
+            dx.copy_(hx, non_blocking=True)
+            dm.copy_(hm, non_blocking=True)
+            dh.copy_(hh, non_blocking=True)
+            t = gblod.build_lod(dx, dm, dh, n_max=n_max, seed=1)
+            for cam in cams:
+                im, _ = r.render(t, cam, par, image=img, accum=acc)
+                out_h.copy_(im, non_blocking=True)
+            torch.cuda.synchronize()
+            t.free()
+
+        for _ in range(1):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": None, "unit": "frames/s", "h2d_bytes_per_step": int(p.xyz.nbytes + p.mass.nbytes + p.h.nbytes),
+               "d2h_bytes_per_step": int(nf * W * H), "_s": e2e_s}
+
+    # reduce over ranks: slowest time, all frames
+    if world > 1:
+        t = torch.tensor([tot_ms, e2e["_s"] if e2e else 0.0], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms, e2e_max = float(t[0]), float(t[1])
+        if e2e:
+            e2e["_s"] = e2e_max
+    frames_all = world * a.steps * nf
+    value = frames_all / (tot_ms / 1e3)
+    if e2e:
+        e2e["value"] = frames_all / e2e.pop("_s")
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    splat_ms, splat_launches = pr
+    achieved = OPS_PER_PIXEL_UPDATE * upd / (splat_ms / 1e3) / 1e12 if splat_ms > 0 else 0.0
+    peak = SMS * LANES * SM_MAX_MHZ * 1e6 / 1e12
+    lod_frame_s = np.sum(frame_ms) / 1e3
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "frames/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": tot_ms / a.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 projection, u64 fixed-point accumulation, f64 node criterion",
+        "data": "synthetic",
+        "config": {"workload": desc, "particles": p.n, "frames_per_step": nf, "resolution": f"{W}x{H}",
+                   "n_max": n_max, "lambda_px": lam, "kernel": "gaussian, sigma = h, 3-sigma support",
+                   "step": "build_lod + every frame at level of detail",
+                   "l2": "flushed between steps (256 MiB write); octree and particles exceed the 129 MB L2",
+                   "octree_nodes": int(info.n_nodes), "octree_points": int(info.n_points)},
+        "lod": {"frames_per_s_excl_build": a.steps * nf / lod_frame_s,
+                "splats_per_s": a.steps * lod_counts["splats"] / (tot_ms / 1e3),
+                "p50_ms": float(np.percentile(frame_ms, 50)), "p99_ms": float(np.percentile(frame_ms, 99)),
+                "points_per_frame": lod_counts["points"] / nf, "splats_per_frame": lod_counts["splats"] / nf,
+                "nodes_per_frame": lod_counts["nodes"] / nf,
+                "pixel_updates_per_frame": lod_counts["pixel_updates"] / nf},
+        "build": {"ms": float(np.median(build_ms)), "particles_per_s": p.n / (np.median(build_ms) / 1e3)},
+        "all_points": brute,
+        "clocks": ck,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "k_splat_tiles (R3)", "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak if peak else None, "traffic": None,
+                     "launches": int(splat_launches), "avg_launch_ms": splat_ms / max(splat_launches, 1),
+                     "peak_note": "152 SMs x 128 lanes x 2070 MHz (no measured ALU peak in MEASURED_PEAKS.json)"},
+    }
+    if not a.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(p, cams, n_max)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ the oracle (CPU)
+
+def cpu_baseline(p, cams, n_max, frame_steps: int = 1):
+    """Oracle build of the full particle set + LOD render of one frame, extrapolated to a step."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    T = O.build_tree(p.xyz, p.mass, p.h, seed=1, n_max=n_max)
+    t_build = time.perf_counter() - t0
+    k = len(cams) // 2
+    rp = O.rparams(lambda_px=math.sqrt(n_max))
+    t0 = time.perf_counter()
+    for _ in range(frame_steps):
+        O.render_lod(T, cams[k], rp)
+    t_frame = (time.perf_counter() - t0) / frame_steps
+    nf = len(cams)
+    return {"value": nf / (t_build + nf * t_frame), "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"one oracle build of all {p.n} particles ({t_build:.1f} s) + LOD frame {k} of the path "
+                      f"({t_frame:.1f} s), extrapolated to build + {nf} frames"}
+
+
+def run_reference(a):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    p, cams, n_max, desc = workload(a.workload, a.frames)
+    t0 = time.perf_counter()
+    T = O.build_tree(p.xyz, p.mass, p.h, seed=1, n_max=n_max)
+    t_build = time.perf_counter() - t0
+    rp = O.rparams(lambda_px=math.sqrt(n_max))
+    nf = len(cams)
+    order = [(nf // 2 + 37 * i) % nf for i in range(a.warmup + a.steps)]
+    for i in range(a.warmup):
+        O.render_lod(T, cams[order[i]], rp)
+    ts = []
+    for i in range(a.steps):
+        t0 = time.perf_counter()
+        O.render_lod(T, cams[order[a.warmup + i]], rp)
+        ts.append(time.perf_counter() - t0)
+    t_frame = float(np.mean(ts))
+    value = nf / (t_build + nf * t_frame)
+    sample = (f"oracle (plain C, 1 thread): one build of all {p.n} particles ({t_build:.1f} s) and one LOD frame "
+              f"per step ({t_frame:.1f} s mean over {a.steps} frames), extrapolated to build + {nf} frames")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": (t_build + nf * t_frame) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 oracle, f32 projection",
+            "data": "synthetic", "config": {"workload": desc, "particles": p.n, "frames_per_step": nf,
+                                            "n_max": n_max},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args_()
+    if a.warmup < 3:
+        a.warmup = 3
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -157,7 +157,8 @@ typedef struct {
     double tone_lo, tone_hi; /* fixed log range in intensity units (used when tone_auto == 0) */
     int32_t kernel;       /* GBLOD_KERNEL_* */
     int32_t tone_auto;    /* 1: hi = image maximum, lo = 1e-4 hi */
-    int32_t tile_w, tile_h; /* screen tile in pixels (0 = 16); any value gives the same image */
+    int32_t tile_w, tile_h; /* screen tile, 1..64 each and at most 1024 pixels (0 = 16); any
+                             value gives the same image */
 } gblod_render_params;
 
 /* Render workspace: scratch buffers (grown on demand through the allocator), the sticky
@@ -187,6 +188,8 @@ typedef struct {
     uint64_t pairs;          /* (tile, splat) records */
     uint64_t tiles;
     uint64_t amplitude_lo, amplitude_hi; /* sum of drawn amplitudes */
+    uint64_t pixel_updates;  /* (splat, pixel) pairs inside the kernel support */
+    uint64_t pixel_updates_total; /* the same, summed over every frame of this renderer */
 } gblod_frame_stats;
 
 /* Waits for `stream`, then reports the sticky device status (GBLOD_OK or GBLOD_ERR_RANGE /

@@ -50,8 +50,8 @@ gblod_render_params check_params(const gblod_render_params *p)
     if (std::isnan(q.lambda_px)) fail(GBLOD_ERR_INVALID_ARG, "lambda_px is NaN");
     if (q.tile_w == 0) q.tile_w = 16;
     if (q.tile_h == 0) q.tile_h = 16;
-    if (q.tile_w < 1 || q.tile_h < 1 || q.tile_w > 64 || q.tile_h > 64 || q.tile_w * q.tile_h > 4096)
-        fail(GBLOD_ERR_INVALID_ARG, "tile must be 1..64 x 1..64 with at most 4096 pixels");
+    if (q.tile_w < 1 || q.tile_h < 1 || q.tile_w > 64 || q.tile_h > 64 || q.tile_w * q.tile_h > 1024)
+        fail(GBLOD_ERR_INVALID_ARG, "tile must be 1..64 x 1..64 with at most 1024 pixels");
     if (!q.tone_auto && !(q.tone_hi > q.tone_lo && q.tone_lo > 0.0 && std::isfinite(q.tone_hi)))
         fail(GBLOD_ERR_INVALID_ARG, "fixed tone range needs 0 < tone_lo < tone_hi < inf");
     return q;
@@ -212,6 +212,8 @@ gblod_status gblod_renderer_stats(gblod_renderer *r, void *stream, gblod_frame_s
         out->tiles = h->tiles;
         out->amplitude_lo = h->amp_lo;
         out->amplitude_hi = h->amp_hi;
+        out->pixel_updates = h->pixel_updates;
+        out->pixel_updates_total = h->pixel_updates_total;
     });
 }
 

@@ -8,6 +8,7 @@
 // and every pixel is an exact 64-bit integer sum, so the image does not depend on launch
 // shape, tiling or the order in which splats are added.
 #include <cmath>
+#include <cstddef>
 #include <mutex>
 #include <vector>
 
@@ -510,49 +511,99 @@ __global__ void k_fill_items(uint32_t ntiles, const uint32_t *tile_cnt, const ui
 }
 
 // ------------------------------------------------------------------ R3
+// One block per work item (a tile and up to ITEM of its records).  Every thread owns up to
+// SPLAT_PPT pixels of the tile and keeps their sums in registers; records are staged through
+// shared memory and read by all threads (broadcast), so there are no atomics until each pixel's
+// partial sum is added to the image once.  The table test (q S) >> 37 < 1024 is evaluated as the
+// equivalent q < floor((2^47 - 1) / S) + 1, so pixels outside the support cost one compare.
+constexpr int SPLAT_PPT = 4; // tiles up to 4 * RT = 1024 pixels
+
 __global__ void __launch_bounds__(RT) k_splat_tiles(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
-                                                    Proj P, unsigned long long *__restrict__ img)
+                                                    Proj P, unsigned long long *__restrict__ img,
+                                                    FrameStatsDev *stats)
 {
-    extern __shared__ unsigned long long acc[]; // TW * TH
+    unsigned hits = 0;
     __shared__ int32_t K[1024];
-    const int npix = P.TW * P.TH;
+    __shared__ int4 sA[RT];                 // U, V, S, Wq low word
+    __shared__ unsigned long long sQ[RT];   // q limit
+    __shared__ uint32_t sWh[RT];            // Wq high word
     for (int i = threadIdx.x; i < 1024; i += RT) K[i] = g_ktab[P.kernel][i];
-    for (int i = threadIdx.x; i < npix; i += RT) acc[i] = 0ull;
-    __syncthreads();
     const uint4 it = items[blockIdx.x];
     const int tx = (int)(it.x % (uint32_t)P.tiles_x), ty = (int)(it.x / (uint32_t)P.tiles_x);
     const int X0 = tx * P.TW, Y0 = ty * P.TH;
-    const int X1 = min(X0 + P.TW, P.W) - 1, Y1 = min(Y0 + P.TH, P.H) - 1;
-    for (uint32_t r = it.y + threadIdx.x; r < it.z; r += RT) {
-        const uint4 R = rec[r];
-        const int U = (int)R.x, V = (int)R.y;
-        const uint32_t S = R.z;
-        const unsigned long long Wq = __float2ull_rn(__uint_as_float(R.w));
-        int x0, x1, y0, y1;
-        splat_box(U, V, S, P.W, P.H, x0, x1, y0, y1);
-        x0 = max(x0, X0);
-        x1 = min(x1, X1);
-        y0 = max(y0, Y0);
-        y1 = min(y1, Y1);
-        for (int py = y0; py <= y1; ++py) {
-            const int dy = py * 256 + 128 - V;
-            const long long dy2 = (long long)dy * dy;
-            for (int px = x0; px <= x1; ++px) {
-                const int dx = px * 256 + 128 - U;
-                const unsigned long long q = (unsigned long long)((long long)dx * dx + dy2);
-                const unsigned long long t = (q * (unsigned long long)S) >> 37;
-                if (t < 1024ull) {
-                    const unsigned long long c = (Wq * (unsigned long long)(uint32_t)K[t]) >> 16;
-                    atomicAdd(&acc[(py - Y0) * P.TW + (px - X0)], c);
+    const int npix = P.TW * P.TH;
+    int px256[SPLAT_PPT], py256[SPLAT_PPT];
+    unsigned long long acc[SPLAT_PPT];
+#pragma unroll
+    for (int k = 0; k < SPLAT_PPT; ++k) {
+        const int p = threadIdx.x + k * RT;
+        const int lx = p % P.TW, ly = p / P.TW;
+        px256[k] = (X0 + lx) * 256 + 128;
+        py256[k] = (Y0 + ly) * 256 + 128;
+        acc[k] = 0ull;
+    }
+    const int ppt = (npix + RT - 1) / RT;
+    for (uint32_t base = it.y; base < it.z; base += RT) {
+        __syncthreads();
+        const uint32_t r = base + threadIdx.x;
+        if (r < it.z) {
+            const uint4 R = rec[r];
+            const unsigned long long Wq = __float2ull_rn(__uint_as_float(R.w));
+            sA[threadIdx.x] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)Wq);
+            sWh[threadIdx.x] = (uint32_t)(Wq >> 32);
+            sQ[threadIdx.x] = (140737488355327ull / (unsigned long long)R.z) + 1ull;
+        }
+        __syncthreads();
+        const int nb = (int)min((uint32_t)RT, it.z - base);
+        if (ppt == 1) {
+            const int pxv = px256[0], pyv = py256[0];
+            unsigned long long a0 = acc[0];
+#pragma unroll 4
+            for (int j = 0; j < nb; ++j) {
+                const int4 A = sA[j];
+                const int dx = pxv - A.x, dy = pyv - A.y;
+                const unsigned long long q = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
+                if (q < sQ[j]) {
+                    const unsigned long long t = (q * (unsigned long long)(uint32_t)A.z) >> 37;
+                    const unsigned long long W = ((unsigned long long)sWh[j] << 32) | (uint32_t)A.w;
+                    a0 += (W * (unsigned long long)(uint32_t)K[t]) >> 16;
+                    ++hits;
+                }
+            }
+            acc[0] = a0;
+        } else {
+            for (int j = 0; j < nb; ++j) {
+                const int4 A = sA[j];
+                const unsigned long long QL = sQ[j];
+                const unsigned long long W = ((unsigned long long)sWh[j] << 32) | (uint32_t)A.w;
+#pragma unroll
+                for (int k = 0; k < SPLAT_PPT; ++k) {
+                    if (k < ppt) {
+                        const int dx = px256[k] - A.x, dy = py256[k] - A.y;
+                        const unsigned long long q = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
+                        if (q < QL) {
+                            const unsigned long long t = (q * (unsigned long long)(uint32_t)A.z) >> 37;
+                            acc[k] += (W * (unsigned long long)(uint32_t)K[t]) >> 16;
+                            ++hits;
+                        }
+                    }
                 }
             }
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < npix; i += RT) {
-        const unsigned long long v = acc[i];
-        const int gx = X0 + i % P.TW, gy = Y0 + i / P.TW;
-        if (v && gx < P.W && gy < P.H) atomicAdd(&img[(size_t)gy * P.W + gx], v);
+#pragma unroll
+    for (int k = 0; k < SPLAT_PPT; ++k) {
+        const int p = threadIdx.x + k * RT;
+        if (k < ppt && p < npix && acc[k]) {
+            const int gx = X0 + p % P.TW, gy = Y0 + p / P.TW;
+            if (gx < P.W && gy < P.H) atomicAdd(&img[(size_t)gy * P.W + gx], acc[k]);
+        }
+    }
+    unsigned long long h64 = hits;
+    for (int d = 16; d > 0; d >>= 1) h64 += __shfl_xor_sync(0xffffffffu, h64, d);
+    if ((threadIdx.x & 31) == 0 && h64) {
+        atomicAdd(&stats->pixel_updates, h64);
+        atomicAdd(&stats->pixel_updates_total, h64);
     }
 }
 
@@ -666,9 +717,8 @@ void frame_common(gblod_renderer *r, const Src &src, const Proj &P, const gblod_
         img = r->accum.p;
     }
     GB_CUDA(cudaMemsetAsync(img, 0, npix * 8, s));
-    const size_t smem = (size_t)P.TW * P.TH * 8;
-    launch(GBLOD_K_SPLAT, k_splat_tiles, dim3(nitems), dim3(RT), smem, s, (const uint4 *)r->records.p,
-           (const uint4 *)r->items.p, P, img);
+    launch(GBLOD_K_SPLAT, k_splat_tiles, dim3(nitems), dim3(RT), 0, s, (const uint4 *)r->records.p,
+           (const uint4 *)r->items.p, P, img, r->stats);
     if (image) {
         r->maxv.ensure(A, 1, s);
         double lo = 0.0, hi = 0.0;
@@ -727,7 +777,7 @@ void render_lod(gblod_renderer *r, const gblod_octree *o, const gblod_camera &ca
     r->last_was_lod = true;
     const Allocator &A = r->A;
     const Proj P = make_proj(cam, rp);
-    GB_CUDA(cudaMemsetAsync(r->stats, 0, sizeof(FrameStatsDev), s));
+    GB_CUDA(cudaMemsetAsync(r->stats, 0, offsetof(FrameStatsDev, pixel_updates_total), s));
     const uint64_t nn = o->n_nodes;
     const int levels = o->depth_max + 1;
     r->frontA.ensure(A, nn + 1, s);
@@ -764,7 +814,7 @@ void render_brute(gblod_renderer *r, const float *xyz, const float *mass, const 
     r->last_stream = s;
     r->last_was_lod = false;
     const Proj P = make_proj(cam, rp);
-    GB_CUDA(cudaMemsetAsync(r->stats, 0, sizeof(FrameStatsDev), s));
+    GB_CUDA(cudaMemsetAsync(r->stats, 0, offsetof(FrameStatsDev, pixel_updates_total), s));
     const unsigned long long pts[1] = {n};
     GB_CUDA(cudaMemcpyAsync(&r->stats->points, pts, 8, cudaMemcpyHostToDevice, s));
     SrcFlat src{xyz, mass, h, n};

@@ -6,6 +6,8 @@
 namespace gb {
 struct FrameStatsDev {
     unsigned long long nodes_selected, points, splats, pairs, tiles, amp_lo, amp_hi, items;
+    unsigned long long pixel_updates;       // (splat, pixel) contributions of the last frame
+    unsigned long long pixel_updates_total; // since the renderer was created (never reset)
 };
 } // namespace gb
 

@@ -58,7 +58,7 @@ class OctreeInfo(C.Structure):
 class FrameStats(C.Structure):
     _fields_ = [("nodes_selected", C.c_uint64), ("points", C.c_uint64), ("splats", C.c_uint64),
                 ("pairs", C.c_uint64), ("tiles", C.c_uint64), ("amplitude_lo", C.c_uint64),
-                ("amplitude_hi", C.c_uint64)]
+                ("amplitude_hi", C.c_uint64), ("pixel_updates", C.c_uint64), ("pixel_updates_total", C.c_uint64)]
 
 
 class Allocator(C.Structure):

@@ -30,8 +30,18 @@ def compare_trees(ex: dict, ot: "O.OracleTree"):
     assert np.array_equal(ex["skey"], ot.skey), "sorted keys differ"
     assert np.array_equal(ex["sidx"], ot.sidx), "sort permutation differs"
     assert np.array_equal(ex["pt_src"], ot.pt_src), "representative choice differs"
-    assert np.array_equal(ex["pts4"].view(np.uint32), ot.pts4.view(np.uint32)), "stored points differ"
-    assert np.array_equal(ex["hs"].view(np.uint32), ot.hs.view(np.uint32)), "stored smoothing lengths differ"
+    assert same_floats(ex["pts4"], ot.pts4), "stored points differ"
+    assert same_floats(ex["hs"], ot.hs), "stored smoothing lengths differ"
+
+
+def same_floats(a, b) -> bool:
+    """Bit-identical, except that any two NaNs count as equal (a NaN's payload is not part of the
+    result: fp32 multiplies on the GPU return the canonical NaN, CPUs propagate the input's)."""
+    a, b = np.asarray(a), np.asarray(b)
+    if a.shape != b.shape:
+        return False
+    na, nb = np.isnan(a), np.isnan(b)
+    return bool(np.array_equal(na, nb) and np.array_equal(a[~na].view(np.uint32), b[~nb].view(np.uint32)))
 
 
 def u8_close(a, b, tol=1):

@@ -42,8 +42,10 @@ def test_projection_stage(G):
     n = 20000
     pts = np.concatenate([rng.uniform(-0.2, 1.2, (n, 3)), np.exp(rng.uniform(-4, 4, (n, 1)))], 1).astype(np.float32)
     h = np.exp(rng.uniform(-9, 0, n)).astype(np.float32)
-    pts[:4, 3] = [np.nan, -1.0, 1e30, 0.0]
     cam = _cams()["inside"]
+    ahead = np.asarray(cam["eye"]) + 0.3 * np.asarray(cam["fwd"])  # certainly on screen
+    pts[:4, :3] = ahead
+    pts[:4, 3] = [np.nan, -1.0, 1e30, 0.0]
     for kernel in (0, 1):
         rp = G.make_params(kernel=kernel)
         got = G.project(*to_dev(pts, h), cam, rp).cpu().numpy()
@@ -99,7 +101,7 @@ def test_full_depth_lod_equals_bruteforce(G, R):
         assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("tile", [(8, 8), (32, 8), (32, 16), (1, 1), (64, 64), (13, 7)])
+@pytest.mark.parametrize("tile", [(8, 8), (32, 8), (32, 16), (1, 1), (32, 32), (64, 16), (13, 7)])
 def test_tiling_does_not_change_the_image(G, R, tile):
     p = synth.tiny(30000, seed=24)
     cam = _cams()["inside"]
@@ -162,6 +164,8 @@ def test_invalid_arguments(G, R):
     assert e.value.code == G.ERR_INVALID_ARG
     with pytest.raises(G.GblodError):
         R.render_bruteforce(*to_dev(p.xyz, p.mass, p.h), _cams()["outside"], G.make_params(tile_w=65))
+    with pytest.raises(G.GblodError):
+        R.render_bruteforce(*to_dev(p.xyz, p.mass, p.h), _cams()["outside"], G.make_params(tile_w=64, tile_h=64))
     with pytest.raises(G.GblodError):
         R.render_bruteforce(*to_dev(p.xyz, p.mass, p.h), _cams()["outside"], G.make_params(sigma_min_px=0.0))
 
