@@ -40,22 +40,23 @@ def args_():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["mid", "paper", "tiny"], default="mid")
     ap.add_argument("--frames", type=int, default=0, help="frames per step (0 = the workload's path)")
+    ap.add_argument("--particles", type=int, default=0, help="particles (0 = the workload's size)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-brute", action="store_true")
     return ap.parse_args()
 
 
-def workload(name: str, frames: int):
+def workload(name: str, frames: int, particles: int = 0):
     from paper_0811_2055_gb300 import synth
     if name == "mid":
-        p = synth.mid()
+        p = synth.mid(particles) if particles else synth.mid()
         nf = frames or 240
         cams = [synth.helix_view(k * 240 // nf) for k in range(nf)]
-        desc = ("mid: 2^24 particles (4096 NFW halos, dN/dM ~ M^-1.9, c in [5,15], + 10% uniform), n_max 16000, "
+        desc = (f"mid: {p.n} particles (NFW halos, dN/dM ~ M^-1.9, c in [5,15], + 10% uniform), n_max 16000, "
                 f"{nf}-frame 1920x1080 helical fly-through")
     elif name == "paper":
-        p = synth.paper_scale()
+        p = synth.paper_scale(particles) if particles else synth.paper_scale()
         nf = frames or 8
         cams = [synth.paper_view(j % 8) for j in range(nf)]
         desc = ("paper: 150M particles (65,536 NFW halos + central halo with 30% + 10% uniform), n_max 16000, "
@@ -136,7 +137,7 @@ def run_ours(a):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    p, cams, n_max, desc = workload(a.workload, a.frames)
+    p, cams, n_max, desc = workload(a.workload, a.frames, a.particles)
     W, H = cams[0]["width"], cams[0]["height"]
     xyz, mass, h = (torch.from_numpy(x).to(dev) for x in (p.xyz, p.mass, p.h))
     r = gblod.Renderer()
@@ -359,7 +360,7 @@ def run_reference(a):
     if rank != 0:
         return
     from oracle import oracle as O
-    p, cams, n_max, desc = workload(a.workload, a.frames)
+    p, cams, n_max, desc = workload(a.workload, a.frames, a.particles)
     t0 = time.perf_counter()
     T = O.build_tree(p.xyz, p.mass, p.h, seed=1, n_max=n_max)
     t_build = time.perf_counter() - t0

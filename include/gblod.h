@@ -159,6 +159,9 @@ typedef struct {
     int32_t tone_auto;    /* 1: hi = image maximum, lo = 1e-4 hi */
     int32_t tile_w, tile_h; /* screen tile, 1..64 each and at most 1024 pixels (0 = 16); any
                              value gives the same image */
+    uint64_t record_budget; /* most (tile, splat) records held at once (16 bytes each); 0 = 2^28,
+                             capped at 2^31.  A frame needing more is binned and splatted in
+                             several passes over ranges of its points, with the same image */
 } gblod_render_params;
 
 /* Render workspace: scratch buffers (grown on demand through the allocator), the sticky
@@ -203,6 +206,36 @@ gblod_status gblod_renderer_stats(gblod_renderer *r, void *stream, gblod_frame_s
  * Waits for `stream`. */
 gblod_status gblod_renderer_last_selection(gblod_renderer *r, void *stream, uint32_t *h_nodes, uint64_t cap,
                                            uint64_t *count);
+
+/* ----------------------------------------------------------------- fixed-scratch variant */
+/* Brute-force frame that allocates no memory.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- host applications that own the whole
+ * device memory budget and hand this library only its input and output buffers, plug-ins whose
+ * host forbids device allocation, and real-time loops that must not call cudaMalloc/cudaFree
+ * because those calls can block or synchronise the device.
+ *
+ * Same arguments, results and semantics as gblod_render_bruteforce (identical fixed-point image),
+ * except:
+ *   - d_accum is required (the caller owns the height x width uint64 output); d_image may be NULL;
+ *   - scratch is one statically sized device array inside this library, GBLOD_NOALLOC_SCRATCH_BYTES
+ *     bytes, which every GPU that loads the library holds until the process exits;
+ *   - the first call on a device also performs that device's set-up (resolves the array's device
+ *     address and uploads the kernel table); make that first call before any stream capture;
+ *   - frames are limited to GBLOD_NOALLOC_MAX_TILES screen tiles (e.g. 2048 x 2048 pixels with
+ *     16 x 16 tiles; larger images are rejected with GBLOD_ERR_INVALID_ARG) and to
+ *     GBLOD_NOALLOC_MAX_RECORDS (tile, splat) records (a frame that needs more returns
+ *     GBLOD_ERR_RANGE before anything is splatted; d_accum is then left unspecified);
+ *   - every call shares the one array, so calls that overlap on the GPU (on different streams, or
+ *     from different host threads) race and corrupt each other: serialise them;
+ *   - the fixed-point range checks are returned directly (GBLOD_ERR_RANGE) since there is no
+ *     renderer object to hold a status word; the frame is still completed without the dropped
+ *     splats.  The call waits once on `stream` mid-frame, like gblod_render_bruteforce. */
+#define GBLOD_NOALLOC_MAX_TILES 16384u
+#define GBLOD_NOALLOC_MAX_RECORDS 2097152u
+#define GBLOD_NOALLOC_SCRATCH_BYTES 34227456u /* 32.6 MiB */
+gblod_status gblod_render_bruteforce_noalloc(const float *d_xyz, const float *d_mass, const float *d_h, uint64_t n,
+                                             const gblod_camera *camera, const gblod_render_params *params,
+                                             uint8_t *d_image, uint64_t *d_accum, void *stream);
 
 /* ----------------------------------------------------------------- stage entry points */
 /* A1 alone: 63-bit Morton keys of n points (octree paragraph; q = clamp(floor((x - lo) 2^21 /

@@ -175,6 +175,21 @@ gblod_status gblod_render_bruteforce(gblod_renderer *r, const float *d_xyz, cons
     });
 }
 
+gblod_status gblod_render_bruteforce_noalloc(const float *d_xyz, const float *d_mass, const float *d_h, uint64_t n,
+                                             const gblod_camera *camera, const gblod_render_params *params,
+                                             uint8_t *d_image, uint64_t *d_accum, void *stream)
+{
+    gblod_status out = GBLOD_OK;
+    gblod_status st = guarded([&] {
+        if (n > 0 && (!d_xyz || !d_mass || !d_h)) fail(GBLOD_ERR_INVALID_ARG, "particle arrays must not be NULL");
+        check_camera(camera);
+        const gblod_render_params p = check_params(params);
+        out = render_brute_noalloc(d_xyz, d_mass, d_h, n, *camera, p, d_image, d_accum, (cudaStream_t)stream);
+        if (out == GBLOD_ERR_RANGE) set_error("a drawn amplitude or the amplitude sum is out of fixed-point range");
+    });
+    return st != GBLOD_OK ? st : out;
+}
+
 gblod_status gblod_renderer_status(gblod_renderer *r, void *stream, int reset)
 {
     gblod_status out = GBLOD_OK;

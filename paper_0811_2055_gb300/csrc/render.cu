@@ -7,6 +7,7 @@
 // fixed order, positions are quantised to 1/256 px, the kernel is a 1024-entry integer table
 // and every pixel is an exact 64-bit integer sum, so the image does not depend on launch
 // shape, tiling or the order in which splats are added.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <mutex>
@@ -401,13 +402,14 @@ __device__ __forceinline__ void src_load(const SrcFlat &s, unsigned long long e,
 }
 
 template <class Src>
-__global__ void __launch_bounds__(RT) k_project_count(Src src, Proj P, uint32_t *__restrict__ tile_cnt,
+__global__ void __launch_bounds__(RT) k_project_count(Src src, Proj P, unsigned long long e_lo,
+                                                      unsigned long long e_hi, uint32_t *__restrict__ tile_cnt,
                                                       unsigned *status, FrameStatsDev *stats)
 {
-    const unsigned long long total = src_total(src);
+    const unsigned long long total = min(src_total(src), e_hi);
     const int lane = threadIdx.x & 31;
-    unsigned long long splats = 0;
-    for (unsigned long long a = (unsigned long long)blockIdx.x * CHUNK; a < total;
+    unsigned long long splats = 0, pairs = 0;
+    for (unsigned long long a = e_lo + (unsigned long long)blockIdx.x * CHUNK; a < total;
          a += (unsigned long long)gridDim.x * CHUNK) {
         const unsigned long long b = min(total, a + CHUNK);
         uint32_t j0, j1;
@@ -434,6 +436,7 @@ __global__ void __launch_bounds__(RT) k_project_count(Src src, Proj P, uint32_t 
                 splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
                 if (x0 <= x1 && y0 <= y1) {
                     const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
+                    pairs += (unsigned long long)(tx1 - tx0 + 1) * (unsigned long long)(ty1 - ty0 + 1);
                     for (int ty = ty0; ty <= ty1; ++ty)
                         for (int tx = tx0; tx <= tx1; ++tx) {
                             const uint32_t t = (uint32_t)(ty * P.tiles_x + tx);
@@ -446,18 +449,23 @@ __global__ void __launch_bounds__(RT) k_project_count(Src src, Proj P, uint32_t 
             }
         }
     }
-    for (int d = 16; d > 0; d >>= 1) splats += __shfl_xor_sync(0xffffffffu, splats, d);
+    for (int d = 16; d > 0; d >>= 1) {
+        splats += __shfl_xor_sync(0xffffffffu, splats, d);
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, d);
+    }
     if (lane == 0 && splats) atomicAdd(&stats->splats, splats);
+    if (lane == 0 && pairs) atomicAdd(&stats->pairs, pairs);
 }
 
 template <class Src>
-__global__ void __launch_bounds__(RT) k_project_scatter(Src src, Proj P, uint32_t *__restrict__ cursor,
+__global__ void __launch_bounds__(RT) k_project_scatter(Src src, Proj P, unsigned long long e_lo,
+                                                        unsigned long long e_hi, uint32_t *__restrict__ cursor,
                                                         uint4 *__restrict__ rec)
 {
-    const unsigned long long total = src_total(src);
+    const unsigned long long total = min(src_total(src), e_hi);
     const int lane = threadIdx.x & 31;
     const uint32_t lt = gbd::lanemask_lt();
-    for (unsigned long long a = (unsigned long long)blockIdx.x * CHUNK; a < total;
+    for (unsigned long long a = e_lo + (unsigned long long)blockIdx.x * CHUNK; a < total;
          a += (unsigned long long)gridDim.x * CHUNK) {
         const unsigned long long b = min(total, a + CHUNK);
         uint32_t j0, j1;
@@ -675,6 +683,57 @@ __global__ void k_morton_plain(const float *xyz, size_t n, double lx, double ly,
 }
 
 // ------------------------------------------------------------------ frame driver
+// A frame is binned and splatted in one pass when its (tile, splat) records fit the record
+// budget; otherwise the projected points are split into ranges whose records fit, each range is
+// binned and splatted on its own, and the integer partial images add up to the same image.
+constexpr unsigned long long RECORD_BUDGET_DEFAULT = 1ull << 28; // 4 GiB of records
+constexpr unsigned long long RECORD_BUDGET_MAX = 1ull << 31;     // offsets stay 32-bit
+
+struct PassCounts {
+    unsigned long long pairs, points;
+    uint32_t items;
+};
+
+template <class Src>
+PassCounts bin_count(gblod_renderer *r, const Src &src, const Proj &P, unsigned long long lo, unsigned long long hi,
+                     FrameStatsDev *stats, cudaStream_t s)
+{
+    const Allocator &A = r->A;
+    const uint32_t ntiles = (uint32_t)(P.tiles_x * P.tiles_y);
+    GB_CUDA(cudaMemsetAsync(r->tile_cnt.p, 0, (size_t)ntiles * 4, s));
+    const unsigned G = (unsigned)persistent_blocks(4);
+    launch(GBLOD_K_PROJECT_COUNT, k_project_count<Src>, dim3(G), dim3(RT), 0, s, src, P, lo, hi, r->tile_cnt.p,
+           r->status, stats);
+    scan_exclusive_u32(A, r->scan, r->tile_cnt.p, r->tile_off.p, ntiles, r->tile_off.p + ntiles, s);
+    launch(GBLOD_K_RENDER_OTHER, k_tile_items, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
+           (const uint32_t *)r->tile_cnt.p, r->item_cnt.p);
+    scan_exclusive_u32(A, r->scan, r->item_cnt.p, r->item_off.p, ntiles, r->item_off.p + ntiles, s);
+    unsigned long long *h = static_cast<unsigned long long *>(r->hs.get(32));
+    GB_CUDA(cudaMemcpyAsync(h, &stats->pairs, 8, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(h + 1, &stats->points, 8, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(h + 2, r->item_off.p + ntiles, 4, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    return PassCounts{h[0], h[1], (uint32_t)(h[2] & 0xFFFFFFFFull)};
+}
+
+template <class Src>
+void bin_splat(gblod_renderer *r, const Src &src, const Proj &P, unsigned long long lo, unsigned long long hi,
+               const PassCounts &pc, unsigned long long *img, cudaStream_t s)
+{
+    const Allocator &A = r->A;
+    const uint32_t ntiles = (uint32_t)(P.tiles_x * P.tiles_y);
+    r->records.ensure(A, pc.pairs, s);
+    r->items.ensure(A, pc.items, s);
+    GB_CUDA(cudaMemcpyAsync(r->tile_cur.p, r->tile_off.p, (size_t)ntiles * 4, cudaMemcpyDeviceToDevice, s));
+    launch(GBLOD_K_PROJECT_SCATTER, k_project_scatter<Src>, dim3((unsigned)persistent_blocks(4)), dim3(RT), 0, s, src,
+           P, lo, hi, r->tile_cur.p, r->records.p);
+    launch(GBLOD_K_RENDER_OTHER, k_fill_items, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
+           (const uint32_t *)r->tile_cnt.p, (const uint32_t *)r->tile_off.p, (const uint32_t *)r->item_off.p,
+           r->items.p);
+    launch(GBLOD_K_SPLAT, k_splat_tiles, dim3(pc.items), dim3(RT), 0, s, (const uint4 *)r->records.p,
+           (const uint4 *)r->items.p, P, img, r->stats);
+}
+
 template <class Src>
 void frame_common(gblod_renderer *r, const Src &src, const Proj &P, const gblod_render_params &rp, uint8_t *image,
                   uint64_t *accum, cudaStream_t s)
@@ -686,30 +745,7 @@ void frame_common(gblod_renderer *r, const Src &src, const Proj &P, const gblod_
     r->tile_cur.ensure(A, ntiles, s);
     r->item_cnt.ensure(A, ntiles, s);
     r->item_off.ensure(A, ntiles + 1, s);
-    GB_CUDA(cudaMemsetAsync(r->tile_cnt.p, 0, (size_t)ntiles * 4, s));
-    const unsigned G = (unsigned)persistent_blocks(4);
-    launch(GBLOD_K_PROJECT_COUNT, k_project_count<Src>, dim3(G), dim3(RT), 0, s, src, P, r->tile_cnt.p, r->status,
-           r->stats);
-    scan_exclusive_u32(A, r->scan, r->tile_cnt.p, r->tile_off.p, ntiles, r->tile_off.p + ntiles, s);
-    launch(GBLOD_K_RENDER_OTHER, k_tile_items, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
-           (const uint32_t *)r->tile_cnt.p, r->item_cnt.p);
-    scan_exclusive_u32(A, r->scan, r->item_cnt.p, r->item_off.p, ntiles, r->item_off.p + ntiles, s);
-    // one read-back per frame: the number of (tile, splat) records and work items
-    uint32_t *h = static_cast<uint32_t *>(r->hs.get(16));
-    GB_CUDA(cudaMemcpyAsync(h, r->tile_off.p + ntiles, 4, cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaMemcpyAsync(h + 1, r->item_off.p + ntiles, 4, cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
-    const uint32_t pairs = h[0], nitems = h[1];
-    const unsigned long long pt[2] = {pairs, ntiles};
-    GB_CUDA(cudaMemcpyAsync(&r->stats->pairs, pt, sizeof(pt), cudaMemcpyHostToDevice, s));
-    r->records.ensure(A, pairs, s);
-    r->items.ensure(A, nitems, s);
-    GB_CUDA(cudaMemcpyAsync(r->tile_cur.p, r->tile_off.p, (size_t)ntiles * 4, cudaMemcpyDeviceToDevice, s));
-    launch(GBLOD_K_PROJECT_SCATTER, k_project_scatter<Src>, dim3(G), dim3(RT), 0, s, src, P, r->tile_cur.p,
-           r->records.p);
-    launch(GBLOD_K_RENDER_OTHER, k_fill_items, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
-           (const uint32_t *)r->tile_cnt.p, (const uint32_t *)r->tile_off.p, (const uint32_t *)r->item_off.p,
-           r->items.p);
+    r->pass_stats.ensure(A, 1, s);
     const size_t npix = (size_t)P.W * P.H;
     unsigned long long *img = reinterpret_cast<unsigned long long *>(accum);
     if (!img) {
@@ -717,8 +753,39 @@ void frame_common(gblod_renderer *r, const Src &src, const Proj &P, const gblod_
         img = r->accum.p;
     }
     GB_CUDA(cudaMemsetAsync(img, 0, npix * 8, s));
-    launch(GBLOD_K_SPLAT, k_splat_tiles, dim3(nitems), dim3(RT), 0, s, (const uint4 *)r->records.p,
-           (const uint4 *)r->items.p, P, img, r->stats);
+    const unsigned long long RECORD_BUDGET =
+        rp.record_budget ? std::min<unsigned long long>(rp.record_budget, RECORD_BUDGET_MAX) : RECORD_BUDGET_DEFAULT;
+    // whole frame first; its counts also give the frame statistics
+    const PassCounts all = bin_count(r, src, P, 0ull, ~0ull, r->stats, s);
+    const unsigned long long tl[1] = {ntiles};
+    GB_CUDA(cudaMemcpyAsync(&r->stats->tiles, tl, 8, cudaMemcpyHostToDevice, s));
+    if (all.pairs <= RECORD_BUDGET) {
+        bin_splat(r, src, P, 0ull, ~0ull, all, img, s);
+    } else {
+        // split the point range until every piece's records fit the budget (a single point
+        // may exceed it; its records always fit the 2^31 maximum)
+        const unsigned long long pieces =
+            std::max(1ull, std::min(all.points, (all.pairs + RECORD_BUDGET - 1) / RECORD_BUDGET * 2));
+        std::vector<std::pair<unsigned long long, unsigned long long>> todo;
+        for (unsigned long long k = pieces; k-- > 0;) {
+            const unsigned long long lo = all.points * k / pieces, hi = all.points * (k + 1) / pieces;
+            if (hi > lo) todo.emplace_back(lo, hi);
+        }
+        while (!todo.empty()) {
+            const auto [lo, hi] = todo.back();
+            todo.pop_back();
+            GB_CUDA(cudaMemsetAsync(r->pass_stats.p, 0, sizeof(FrameStatsDev), s));
+            const PassCounts pc = bin_count(r, src, P, lo, hi, r->pass_stats.p, s);
+            if (pc.pairs > RECORD_BUDGET && hi - lo > 1) {
+                const unsigned long long mid = lo + (hi - lo) / 2;
+                todo.emplace_back(mid, hi);
+                todo.emplace_back(lo, mid);
+                continue;
+            }
+            if (pc.pairs > RECORD_BUDGET_MAX) fail(GBLOD_ERR_RANGE, "one point needs more than 2^31 tile records");
+            bin_splat(r, src, P, lo, hi, pc, img, s);
+        }
+    }
     if (image) {
         r->maxv.ensure(A, 1, s);
         double lo = 0.0, hi = 0.0;
@@ -760,6 +827,7 @@ void renderer_release(gblod_renderer *r)
     r->tile_cnt.release(A, s); r->tile_off.release(A, s); r->tile_cur.release(A, s);
     r->item_cnt.release(A, s); r->item_off.release(A, s);
     r->records.release(A, s); r->items.release(A, s); r->accum.release(A, s); r->maxv.release(A, s);
+    r->pass_stats.release(A, s);
     r->scan.buf.release(A, s);
 }
 
@@ -833,6 +901,152 @@ void morton_keys(const float *xyz, uint64_t n, const double lo[3], double side, 
 {
     launch(GBLOD_K_MORTON, k_morton_plain, dim3(persistent_blocks(4)), dim3(256), 0, s, xyz, (size_t)n, lo[0], lo[1],
            lo[2], 2097152.0 / side, keys);
+}
+
+} // namespace gb
+
+// ------------------------------------------------------------------ fixed-scratch brute-force frame
+// For callers that cannot allocate device memory: the scratch of a brute-force frame lives in one
+// file-scope device array of fixed size, and nothing is allocated per call.  Host code must not
+// pass g_noalloc_scratch itself to a kernel (in host code the name is only a stand-in for the
+// device object); its device address is resolved once per device with cudaGetSymbolAddress.
+namespace gb {
+namespace {
+
+constexpr size_t na_align(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t NA_TILES = GBLOD_NOALLOC_MAX_TILES;
+constexpr size_t NA_RECORDS = GBLOD_NOALLOC_MAX_RECORDS;
+constexpr size_t NA_ITEMS = NA_TILES + NA_RECORDS / ITEM;
+constexpr size_t NA_SCAN_BYTES = 65536;
+constexpr size_t NA_OFF_RECORDS = 0;
+constexpr size_t NA_OFF_ITEMS = NA_OFF_RECORDS + na_align(NA_RECORDS * sizeof(uint4));
+constexpr size_t NA_OFF_TILE_CNT = NA_OFF_ITEMS + na_align(NA_ITEMS * sizeof(uint4));
+constexpr size_t NA_OFF_TILE_OFF = NA_OFF_TILE_CNT + na_align(NA_TILES * 4);
+constexpr size_t NA_OFF_TILE_CUR = NA_OFF_TILE_OFF + na_align((NA_TILES + 1) * 4);
+constexpr size_t NA_OFF_ITEM_CNT = NA_OFF_TILE_CUR + na_align(NA_TILES * 4);
+constexpr size_t NA_OFF_ITEM_OFF = NA_OFF_ITEM_CNT + na_align(NA_TILES * 4);
+constexpr size_t NA_OFF_SCAN = NA_OFF_ITEM_OFF + na_align((NA_TILES + 1) * 4);
+constexpr size_t NA_OFF_STATS = NA_OFF_SCAN + na_align(NA_SCAN_BYTES);
+constexpr size_t NA_OFF_STATUS = NA_OFF_STATS + na_align(sizeof(FrameStatsDev));
+constexpr size_t NA_OFF_MAXV = NA_OFF_STATUS + na_align(sizeof(unsigned));
+constexpr size_t NA_BYTES = NA_OFF_MAXV + na_align(sizeof(unsigned long long));
+static_assert(NA_BYTES == GBLOD_NOALLOC_SCRATCH_BYTES, "GBLOD_NOALLOC_SCRATCH_BYTES must match the layout");
+
+} // namespace
+} // namespace gb
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[gb::NA_BYTES];
+
+namespace gb {
+namespace {
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_na_mu;
+unsigned char *g_na_addr[NA_MAX_DEVICES] = {};
+
+// Device address of g_noalloc_scratch on the current device (resolved once per device).
+unsigned char *noalloc_scratch()
+{
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NA_MAX_DEVICES) fail(GBLOD_ERR_INVALID_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> g(g_na_mu);
+    if (!g_na_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        check_cuda(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        if (!p) fail(GBLOD_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
+        g_na_addr[dev] = static_cast<unsigned char *>(p);
+    }
+    return g_na_addr[dev];
+}
+
+} // namespace
+
+gblod_status render_brute_noalloc(const float *xyz, const float *mass, const float *h, uint64_t n,
+                                  const gblod_camera &cam, const gblod_render_params &rp, uint8_t *image,
+                                  uint64_t *accum, cudaStream_t s)
+{
+    check_image(cam);
+    if (!accum) fail(GBLOD_ERR_INVALID_ARG, "gblod_render_bruteforce_noalloc needs d_accum (caller-owned output)");
+    const Proj P = make_proj(cam, rp);
+    const size_t ntiles = (size_t)P.tiles_x * P.tiles_y;
+    if (ntiles > NA_TILES)
+        fail(GBLOD_ERR_INVALID_ARG, "gblod_render_bruteforce_noalloc: " + std::to_string(ntiles) +
+                                        " screen tiles exceed the fixed maximum of " + std::to_string(NA_TILES));
+    ensure_tables();
+    unsigned char *base = noalloc_scratch();
+    uint4 *records = reinterpret_cast<uint4 *>(base + NA_OFF_RECORDS);
+    uint4 *items = reinterpret_cast<uint4 *>(base + NA_OFF_ITEMS);
+    uint32_t *tile_cnt = reinterpret_cast<uint32_t *>(base + NA_OFF_TILE_CNT);
+    uint32_t *tile_off = reinterpret_cast<uint32_t *>(base + NA_OFF_TILE_OFF);
+    uint32_t *tile_cur = reinterpret_cast<uint32_t *>(base + NA_OFF_TILE_CUR);
+    uint32_t *item_cnt = reinterpret_cast<uint32_t *>(base + NA_OFF_ITEM_CNT);
+    uint32_t *item_off = reinterpret_cast<uint32_t *>(base + NA_OFF_ITEM_OFF);
+    FrameStatsDev *stats = reinterpret_cast<FrameStatsDev *>(base + NA_OFF_STATS);
+    unsigned *status = reinterpret_cast<unsigned *>(base + NA_OFF_STATUS);
+    unsigned long long *maxv = reinterpret_cast<unsigned long long *>(base + NA_OFF_MAXV);
+    // the scan helper finds its temp space already large enough and never allocates
+    const Allocator none;
+    ScanTmp scan;
+    scan.buf.p = base + NA_OFF_SCAN;
+    scan.buf.cap = NA_SCAN_BYTES;
+
+    // the array keeps the previous call's contents: clear everything that must start at zero
+    GB_CUDA(cudaMemsetAsync(tile_cnt, 0, ntiles * 4, s));
+    GB_CUDA(cudaMemsetAsync(stats, 0, sizeof(FrameStatsDev), s));
+    GB_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
+    const SrcFlat src{xyz, mass, h, n};
+    const unsigned G = (unsigned)persistent_blocks(4);
+    const uint32_t nt = (uint32_t)ntiles;
+    launch(GBLOD_K_PROJECT_COUNT, k_project_count<SrcFlat>, dim3(G), dim3(RT), 0, s, src, P, 0ull, ~0ull, tile_cnt,
+           status, stats);
+    scan_exclusive_u32(none, scan, tile_cnt, tile_off, ntiles, tile_off + ntiles, s);
+    launch(GBLOD_K_RENDER_OTHER, k_tile_items, dim3((nt + 255) / 256), dim3(256), 0, s, nt,
+           (const uint32_t *)tile_cnt, item_cnt);
+    scan_exclusive_u32(none, scan, item_cnt, item_off, ntiles, item_off + ntiles, s);
+    if (scan.buf.p != base + NA_OFF_SCAN) fail(GBLOD_ERR_CUDA, "scan temp left the fixed scratch");
+
+    // one read-back into host stack memory (no pinned staging buffer is allocated)
+    uint32_t counts[2] = {0, 0};
+    unsigned long long amp_hi = 0, pairs64 = 0;
+    unsigned st_bits = 0;
+    GB_CUDA(cudaMemcpyAsync(&pairs64, &stats->pairs, 8, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(&counts[0], tile_off + ntiles, 4, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(&counts[1], item_off + ntiles, 4, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(&amp_hi, &stats->amp_hi, 8, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(&st_bits, status, 4, cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    const uint32_t nitems = counts[1];
+    if (pairs64 > NA_RECORDS || nitems > NA_ITEMS)
+        fail(GBLOD_ERR_RANGE, "gblod_render_bruteforce_noalloc: the frame needs " + std::to_string(pairs64) +
+                                  " (tile, splat) records, more than the fixed maximum of " +
+                                  std::to_string(NA_RECORDS));
+    GB_CUDA(cudaMemcpyAsync(tile_cur, tile_off, ntiles * 4, cudaMemcpyDeviceToDevice, s));
+    launch(GBLOD_K_PROJECT_SCATTER, k_project_scatter<SrcFlat>, dim3(G), dim3(RT), 0, s, src, P, 0ull, ~0ull,
+           tile_cur, records);
+    launch(GBLOD_K_RENDER_OTHER, k_fill_items, dim3((nt + 255) / 256), dim3(256), 0, s, nt,
+           (const uint32_t *)tile_cnt, (const uint32_t *)tile_off, (const uint32_t *)item_off, items);
+    const size_t npix = (size_t)P.W * P.H;
+    unsigned long long *img = reinterpret_cast<unsigned long long *>(accum);
+    GB_CUDA(cudaMemsetAsync(img, 0, npix * 8, s));
+    launch(GBLOD_K_SPLAT, k_splat_tiles, dim3(nitems), dim3(RT), 0, s, (const uint4 *)records, (const uint4 *)items,
+           P, img, stats);
+    if (image) {
+        double lo = 0.0, hi = 0.0;
+        if (rp.tone_auto) {
+            GB_CUDA(cudaMemsetAsync(maxv, 0, 8, s));
+            launch(GBLOD_K_TONEMAP, k_image_max, dim3(persistent_blocks(2)), dim3(256), 0, s,
+                   (const unsigned long long *)img, npix, maxv);
+        } else {
+            lo = std::ldexp(rp.tone_lo, 32);
+            hi = std::ldexp(rp.tone_hi, 32);
+        }
+        launch(GBLOD_K_TONEMAP, k_tonemap, dim3(persistent_blocks(2)), dim3(256), 0, s,
+               (const unsigned long long *)img, npix, (const unsigned long long *)maxv, rp.tone_auto ? 1 : 0, lo, hi,
+               image);
+    }
+    return (st_bits & ST_RANGE) || amp_hi ? GBLOD_ERR_RANGE : GBLOD_OK;
 }
 
 } // namespace gb

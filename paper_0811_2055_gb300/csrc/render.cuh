@@ -25,6 +25,7 @@ struct gblod_renderer {
     gb::DBuf<uint32_t> tile_cnt, tile_off, tile_cur, item_cnt, item_off;
     gb::DBuf<uint4> records, items;
     gb::DBuf<unsigned long long> accum, maxv;
+    gb::DBuf<gb::FrameStatsDev> pass_stats; // counters of one range when a frame is split
     cudaStream_t last_stream = nullptr;
     bool last_was_lod = false;
 };
@@ -37,6 +38,9 @@ void render_lod(gblod_renderer *r, const gblod_octree *o, const gblod_camera &ca
 void render_brute(gblod_renderer *r, const float *xyz, const float *mass, const float *h, uint64_t n,
                   const gblod_camera &cam, const gblod_render_params &rp, uint8_t *image, uint64_t *accum,
                   cudaStream_t s);
+gblod_status render_brute_noalloc(const float *xyz, const float *mass, const float *h, uint64_t n,
+                                  const gblod_camera &cam, const gblod_render_params &rp, uint8_t *image,
+                                  uint64_t *accum, cudaStream_t s);
 void project_points(const float4 *pts4, const float *h, uint64_t n, const gblod_camera &cam,
                     const gblod_render_params &rp, int64_t *out, cudaStream_t s);
 void morton_keys(const float *xyz, uint64_t n, const double lo[3], double side, uint64_t *keys, cudaStream_t s);

@@ -46,7 +46,8 @@ class Camera(C.Structure):
 class RenderParams(C.Structure):
     _fields_ = [("lambda_px", C.c_double), ("sigma_min_px", C.c_double), ("sigma_max_px", C.c_double),
                 ("tone_lo", C.c_double), ("tone_hi", C.c_double), ("kernel", C.c_int32),
-                ("tone_auto", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32)]
+                ("tone_auto", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
+                ("record_budget", C.c_uint64)]
 
 
 class OctreeInfo(C.Structure):
@@ -134,13 +135,14 @@ def make_camera(cam: dict) -> Camera:
 
 
 def make_params(lambda_px=None, sigma_min_px=0.5, sigma_max_px=128.0, kernel=KERNEL_GAUSSIAN, tone_auto=True,
-                tone_lo=0.0, tone_hi=0.0, tile_w=16, tile_h=16) -> RenderParams:
+                tone_lo=0.0, tone_hi=0.0, tile_w=16, tile_h=16, record_budget=0) -> RenderParams:
     p = RenderParams()
     p.lambda_px = -1.0 if lambda_px is None else float(lambda_px)
     p.sigma_min_px, p.sigma_max_px = float(sigma_min_px), float(sigma_max_px)
     p.tone_lo, p.tone_hi = float(tone_lo), float(tone_hi)
     p.kernel, p.tone_auto = int(kernel), int(bool(tone_auto))
     p.tile_w, p.tile_h = int(tile_w), int(tile_h)
+    p.record_budget = int(record_budget)
     return p
 
 

@@ -111,6 +111,24 @@ def test_tiling_does_not_change_the_image(G, R, tile):
     assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("budget", [50_000, 7_000, 1_500])
+def test_split_frames_give_the_same_image(G, R, budget):
+    """A frame whose records exceed the budget is binned in several passes: same image."""
+    p = synth.tiny(60000, seed=26)
+    d = to_dev(p.xyz, p.mass, p.h)
+    t = G.build_lod(*d, n_max=300, seed=3)
+    for cam in _cams().values():
+        _, a = R.render_bruteforce(*d, cam, G.make_params())
+        pairs = R.stats()["pairs"]
+        _, b = R.render_bruteforce(*d, cam, G.make_params(record_budget=budget))
+        assert pairs > budget and R.stats()["pairs"] == pairs
+        assert torch.equal(a, b)
+        _, c = R.render(t, cam, G.make_params(lambda_px=10.0))
+        s1 = R.stats()
+        _, e = R.render(t, cam, G.make_params(lambda_px=10.0, record_budget=budget))
+        assert torch.equal(c, e) and R.stats() == s1
+
+
 def test_fixed_tone_range(G, R):
     p = synth.tiny(30000, seed=25)
     cam = _cams()["outside"]
