@@ -182,6 +182,7 @@ def run_ours(a):
         torch.cuda.synchronize()
         tot_ms, frame_ms, build_ms = 0.0, [], []
         l0 = gblod.launch_count()
+        upd0 = r.stats()["pixel_updates_total"]
         if probe is not None:
             gblod.probe_enable(probe)
         for _ in range(steps):
@@ -206,7 +207,8 @@ def run_ours(a):
         pr = gblod.probe_read() if probe is not None else None
         if probe is not None:
             gblod.probe_enable(gblod.K_ANY)
-        return tot_ms, frame_ms, build_ms, launches, pr
+        upd = r.stats()["pixel_updates_total"] - upd0
+        return tot_ms, frame_ms, build_ms, launches, pr, upd
 
     # census of one LOD pass and one brute pass (untimed; the counts are deterministic)
     tree = lod_step()
@@ -223,9 +225,8 @@ def run_ours(a):
     assert r.status() == gblod.OK
 
     clocks = Clocks(local)
-    upd0 = r.stats()["pixel_updates_total"]
-    tot_ms, frame_ms, build_ms, launches, pr = timed(lod_step, 2 + 2 * nf, a.steps, a.warmup, probe=gblod.K_SPLAT)
-    upd = r.stats()["pixel_updates_total"] - upd0
+    tot_ms, frame_ms, build_ms, launches, pr, upd = timed(lod_step, 2 + 2 * nf, a.steps, a.warmup,
+                                                          probe=gblod.K_SPLAT)
     ck = clocks.stop()
 
     brute = None
@@ -236,7 +237,7 @@ def run_ours(a):
             s = r.stats()
             b_counts["splats"] += s["splats"]
             b_counts["pixel_updates"] += s["pixel_updates"]
-        b_ms, b_frames, _, _, _ = timed(brute_step, 2 * nf, a.steps, a.warmup)
+        b_ms, b_frames, _, _, _, _ = timed(brute_step, 2 * nf, a.steps, a.warmup)
         brute = dict(frames_per_s=a.steps * nf / (b_ms / 1e3), ms_per_frame=b_ms / (a.steps * nf),
                      splats_per_s=a.steps * b_counts["splats"] / (b_ms / 1e3),
                      points_per_s=a.steps * nf * p.n / (b_ms / 1e3),

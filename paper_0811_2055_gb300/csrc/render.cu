@@ -519,39 +519,70 @@ __global__ void k_fill_items(uint32_t ntiles, const uint32_t *tile_cnt, const ui
 }
 
 // ------------------------------------------------------------------ R3
-// One block per work item (a tile and up to ITEM of its records).  Every thread owns up to
-// SPLAT_PPT pixels of the tile and keeps their sums in registers; records are staged through
-// shared memory and read by all threads (broadcast), so there are no atomics until each pixel's
-// partial sum is added to the image once.  The table test (q S) >> 37 < 1024 is evaluated as the
-// equivalent q < floor((2^47 - 1) / S) + 1, so pixels outside the support cost one compare.
-constexpr int SPLAT_PPT = 4; // tiles up to 4 * RT = 1024 pixels
+// One block per work item (a tile and up to ITEM of its records).  Records are staged through
+// shared memory in batches and split by the size of their box inside the tile:
+//   large  every thread evaluates its own pixel(s) and keeps the sums in registers (gather, no
+//          atomics): efficient when the blob covers most of the tile;
+//   small  one warp per record, lanes enumerate only the box pixels and add into a shared
+//          64-bit tile accumulator: efficient for blobs much smaller than the tile and for the
+//          corners of big blobs.
+// The table test (q S) >> 37 < 1024 is evaluated exactly as q S < 2^47.  At the end each pixel's
+// register and shared partial sums are added to the image once.
+constexpr int SPLAT_PPT = 4;      // tiles up to 4 * RT = 1024 pixels
+constexpr int SMALL_MAX = 128;    // box pixels at or below which a record takes the warp path
+
+__device__ __forceinline__ bool pixel_term(int dx, int dy, uint32_t S, unsigned long long W, const int32_t *K,
+                                           unsigned long long &c)
+{
+    const unsigned long long q = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
+    const unsigned long long p = q * (unsigned long long)S;
+    if (p >= (1ull << 47)) return false;
+    c = (W * (unsigned long long)(uint32_t)K[p >> 37]) >> 16;
+    return true;
+}
 
 __global__ void __launch_bounds__(RT) k_splat_tiles(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
                                                     Proj P, unsigned long long *__restrict__ img,
                                                     FrameStatsDev *stats)
 {
-    unsigned hits = 0;
     __shared__ int32_t K[1024];
-    __shared__ int4 sA[RT];                 // U, V, S, Wq low word
-    __shared__ unsigned long long sQ[RT];   // q limit
-    __shared__ uint32_t sWh[RT];            // Wq high word
+    __shared__ int4 sA[RT];                     // U, V, S, Wq low word
+    __shared__ uint32_t sWh[RT];                // Wq high word
+    __shared__ uint32_t sBox[RT];               // tile-local box: x0 | x1 << 8 | y0 << 16 | y1 << 24
+    __shared__ uint16_t sLarge[RT], sSmall[RT];
+    __shared__ uint8_t sDivQ[33][32], sDivR[33][32];
+    __shared__ unsigned long long sAcc[SPLAT_PPT * RT];
+    __shared__ int nLarge, nSmall;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned hits = 0;
     for (int i = threadIdx.x; i < 1024; i += RT) K[i] = g_ktab[P.kernel][i];
+    for (int i = threadIdx.x; i < 33 * 32; i += RT) {
+        const int w = i / 32, l = i % 32;
+        (&sDivQ[0][0])[i] = (uint8_t)(w ? l / w : 0);
+        (&sDivR[0][0])[i] = (uint8_t)(w ? l % w : 0);
+    }
     const uint4 it = items[blockIdx.x];
     const int tx = (int)(it.x % (uint32_t)P.tiles_x), ty = (int)(it.x / (uint32_t)P.tiles_x);
     const int X0 = tx * P.TW, Y0 = ty * P.TH;
+    const int X1 = min(X0 + P.TW, P.W) - 1, Y1 = min(Y0 + P.TH, P.H) - 1;
     const int npix = P.TW * P.TH;
+    const int ppt = (npix + RT - 1) / RT;
+    for (int i = threadIdx.x; i < SPLAT_PPT * RT; i += RT) sAcc[i] = 0ull;
     int px256[SPLAT_PPT], py256[SPLAT_PPT];
     unsigned long long acc[SPLAT_PPT];
 #pragma unroll
     for (int k = 0; k < SPLAT_PPT; ++k) {
         const int p = threadIdx.x + k * RT;
-        const int lx = p % P.TW, ly = p / P.TW;
-        px256[k] = (X0 + lx) * 256 + 128;
-        py256[k] = (Y0 + ly) * 256 + 128;
+        px256[k] = (X0 + p % P.TW) * 256 + 128;
+        py256[k] = (Y0 + p / P.TW) * 256 + 128;
         acc[k] = 0ull;
     }
-    const int ppt = (npix + RT - 1) / RT;
     for (uint32_t base = it.y; base < it.z; base += RT) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            nLarge = 0;
+            nSmall = 0;
+        }
         __syncthreads();
         const uint32_t r = base + threadIdx.x;
         if (r < it.z) {
@@ -559,57 +590,89 @@ __global__ void __launch_bounds__(RT) k_splat_tiles(const uint4 *__restrict__ re
             const unsigned long long Wq = __float2ull_rn(__uint_as_float(R.w));
             sA[threadIdx.x] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)Wq);
             sWh[threadIdx.x] = (uint32_t)(Wq >> 32);
-            sQ[threadIdx.x] = (140737488355327ull / (unsigned long long)R.z) + 1ull;
+            int x0, x1, y0, y1;
+            splat_box((int)R.x, (int)R.y, R.z, P.W, P.H, x0, x1, y0, y1);
+            x0 = max(x0, X0) - X0;
+            x1 = min(x1, X1) - X0;
+            y0 = max(y0, Y0) - Y0;
+            y1 = min(y1, Y1) - Y0;
+            if (x0 <= x1 && y0 <= y1) {
+                const int bw = x1 - x0 + 1, area = bw * (y1 - y0 + 1);
+                sBox[threadIdx.x] = (uint32_t)x0 | (uint32_t)x1 << 8 | (uint32_t)y0 << 16 | (uint32_t)y1 << 24;
+                if (area <= SMALL_MAX && bw <= 32)
+                    sSmall[atomicAdd(&nSmall, 1)] = (uint16_t)threadIdx.x;
+                else
+                    sLarge[atomicAdd(&nLarge, 1)] = (uint16_t)threadIdx.x;
+            }
         }
         __syncthreads();
-        const int nb = (int)min((uint32_t)RT, it.z - base);
+        const int nl = nLarge, ns = nSmall;
+        // large records: every thread, its own pixels, register sums
         if (ppt == 1) {
             const int pxv = px256[0], pyv = py256[0];
             unsigned long long a0 = acc[0];
-#pragma unroll 4
-            for (int j = 0; j < nb; ++j) {
-                const int4 A = sA[j];
-                const int dx = pxv - A.x, dy = pyv - A.y;
-                const unsigned long long q = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
-                if (q < sQ[j]) {
-                    const unsigned long long t = (q * (unsigned long long)(uint32_t)A.z) >> 37;
-                    const unsigned long long W = ((unsigned long long)sWh[j] << 32) | (uint32_t)A.w;
-                    a0 += (W * (unsigned long long)(uint32_t)K[t]) >> 16;
+            for (int j = 0; j < nl; ++j) {
+                const int q = sLarge[j];
+                const int4 A = sA[q];
+                const unsigned long long W = ((unsigned long long)sWh[q] << 32) | (uint32_t)A.w;
+                unsigned long long c;
+                if (pixel_term(pxv - A.x, pyv - A.y, (uint32_t)A.z, W, K, c)) {
+                    a0 += c;
                     ++hits;
                 }
             }
             acc[0] = a0;
         } else {
-            for (int j = 0; j < nb; ++j) {
-                const int4 A = sA[j];
-                const unsigned long long QL = sQ[j];
-                const unsigned long long W = ((unsigned long long)sWh[j] << 32) | (uint32_t)A.w;
+            for (int j = 0; j < nl; ++j) {
+                const int q = sLarge[j];
+                const int4 A = sA[q];
+                const unsigned long long W = ((unsigned long long)sWh[q] << 32) | (uint32_t)A.w;
 #pragma unroll
                 for (int k = 0; k < SPLAT_PPT; ++k) {
-                    if (k < ppt) {
-                        const int dx = px256[k] - A.x, dy = py256[k] - A.y;
-                        const unsigned long long q = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
-                        if (q < QL) {
-                            const unsigned long long t = (q * (unsigned long long)(uint32_t)A.z) >> 37;
-                            acc[k] += (W * (unsigned long long)(uint32_t)K[t]) >> 16;
-                            ++hits;
-                        }
+                    unsigned long long c;
+                    if (k < ppt && pixel_term(px256[k] - A.x, py256[k] - A.y, (uint32_t)A.z, W, K, c)) {
+                        acc[k] += c;
+                        ++hits;
+                    }
+                }
+            }
+        }
+        // small records: one warp each, lanes over the box pixels, shared accumulation
+        for (int j = warp; j < ns; j += RT / 32) {
+            const int q = sSmall[j];
+            const int4 A = sA[q];
+            const unsigned long long W = ((unsigned long long)sWh[q] << 32) | (uint32_t)A.w;
+            const uint32_t bx = sBox[q];
+            const int x0 = bx & 255, x1 = (bx >> 8) & 255, y0 = (bx >> 16) & 255, y1 = bx >> 24;
+            const int bw = x1 - x0 + 1;
+            const int rows = 32 / bw;
+            const int lx = x0 + sDivR[bw][lane];
+            const int l_row = sDivQ[bw][lane];
+            if (l_row < rows) {
+                const int dx = (X0 + lx) * 256 + 128 - A.x;
+                for (int ly = y0 + l_row; ly <= y1; ly += rows) {
+                    unsigned long long c;
+                    if (pixel_term(dx, (Y0 + ly) * 256 + 128 - A.y, (uint32_t)A.z, W, K, c)) {
+                        atomicAdd(&sAcc[ly * P.TW + lx], c);
+                        ++hits;
                     }
                 }
             }
         }
     }
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < SPLAT_PPT; ++k) {
         const int p = threadIdx.x + k * RT;
-        if (k < ppt && p < npix && acc[k]) {
+        if (k < ppt && p < npix) {
+            const unsigned long long v = acc[k] + sAcc[p];
             const int gx = X0 + p % P.TW, gy = Y0 + p / P.TW;
-            if (gx < P.W && gy < P.H) atomicAdd(&img[(size_t)gy * P.W + gx], acc[k]);
+            if (v && gx < P.W && gy < P.H) atomicAdd(&img[(size_t)gy * P.W + gx], v);
         }
     }
     unsigned long long h64 = hits;
     for (int d = 16; d > 0; d >>= 1) h64 += __shfl_xor_sync(0xffffffffu, h64, d);
-    if ((threadIdx.x & 31) == 0 && h64) {
+    if (lane == 0 && h64) {
         atomicAdd(&stats->pixel_updates, h64);
         atomicAdd(&stats->pixel_updates_total, h64);
     }

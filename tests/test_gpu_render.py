@@ -126,7 +126,9 @@ def test_split_frames_give_the_same_image(G, R, budget):
         _, c = R.render(t, cam, G.make_params(lambda_px=10.0))
         s1 = R.stats()
         _, e = R.render(t, cam, G.make_params(lambda_px=10.0, record_budget=budget))
-        assert torch.equal(c, e) and R.stats() == s1
+        s2 = R.stats()
+        assert torch.equal(c, e)
+        assert all(s1[k] == s2[k] for k in s1 if k != "pixel_updates_total")
 
 
 def test_fixed_tone_range(G, R):
