@@ -519,17 +519,13 @@ __global__ void k_fill_items(uint32_t ntiles, const uint32_t *tile_cnt, const ui
 }
 
 // ------------------------------------------------------------------ R3
-// One block per work item (a tile and up to ITEM of its records).  Records are staged through
-// shared memory in batches and split by the size of their box inside the tile:
-//   large  every thread evaluates its own pixel(s) and keeps the sums in registers (gather, no
-//          atomics): efficient when the blob covers most of the tile;
-//   small  one warp per record, lanes enumerate only the box pixels and add into a shared
-//          64-bit tile accumulator: efficient for blobs much smaller than the tile and for the
-//          corners of big blobs.
-// The table test (q S) >> 37 < 1024 is evaluated exactly as q S < 2^47.  At the end each pixel's
-// register and shared partial sums are added to the image once.
-constexpr int SPLAT_PPT = 4;      // tiles up to 4 * RT = 1024 pixels
-constexpr int SMALL_MAX = 128;    // box pixels at or below which a record takes the warp path
+// One block per work item (a tile and up to ITEM of its records).  The tile is cut into 8 x 4
+// pixel blocks, one lane per pixel; block b belongs to warp b % 8 (up to SPLAT_SLOTS blocks per
+// warp).  Records are staged through shared memory in batches of RT; each warp first compacts,
+// by ballot, the records whose box touches each of its blocks, then evaluates only those for its
+// pixels and keeps the sums in registers (no atomics).  The table test (q S) >> 37 < 1024 is
+// evaluated exactly as q S < 2^47.  Each pixel's sum is added to the image once at the end.
+constexpr int SPLAT_SLOTS = 4; // 8 warps x 4 blocks of 32 pixels: tiles up to 1024 pixels
 
 __device__ __forceinline__ bool pixel_term(int dx, int dy, uint32_t S, unsigned long long W, const int32_t *K,
                                            unsigned long long &c)
@@ -541,134 +537,91 @@ __device__ __forceinline__ bool pixel_term(int dx, int dy, uint32_t S, unsigned 
     return true;
 }
 
-__global__ void __launch_bounds__(RT) k_splat_tiles(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
-                                                    Proj P, unsigned long long *__restrict__ img,
-                                                    FrameStatsDev *stats)
+__global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
+                                                       Proj P, unsigned long long *__restrict__ img,
+                                                       FrameStatsDev *stats)
 {
     __shared__ int32_t K[1024];
-    __shared__ int4 sA[RT];                     // U, V, S, Wq low word
-    __shared__ uint32_t sWh[RT];                // Wq high word
-    __shared__ uint32_t sBox[RT];               // tile-local box: x0 | x1 << 8 | y0 << 16 | y1 << 24
-    __shared__ uint16_t sLarge[RT], sSmall[RT];
-    __shared__ uint8_t sDivQ[33][32], sDivR[33][32];
-    __shared__ unsigned long long sAcc[SPLAT_PPT * RT];
-    __shared__ int nLarge, nSmall;
+    __shared__ int4 sA[RT];                             // U, V, S, Wq low word
+    __shared__ uint32_t sWh[RT];                        // Wq high word
+    __shared__ uint32_t sBox[RT];                       // tile-local box x0 | x1 << 8 | y0 << 16 | y1 << 24
+    __shared__ uint8_t sList[RT / 32][SPLAT_SLOTS][RT]; // per warp and block: records touching it
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = gbd::lanemask_lt();
     unsigned hits = 0;
     for (int i = threadIdx.x; i < 1024; i += RT) K[i] = g_ktab[P.kernel][i];
-    for (int i = threadIdx.x; i < 33 * 32; i += RT) {
-        const int w = i / 32, l = i % 32;
-        (&sDivQ[0][0])[i] = (uint8_t)(w ? l / w : 0);
-        (&sDivR[0][0])[i] = (uint8_t)(w ? l % w : 0);
-    }
     const uint4 it = items[blockIdx.x];
     const int tx = (int)(it.x % (uint32_t)P.tiles_x), ty = (int)(it.x / (uint32_t)P.tiles_x);
     const int X0 = tx * P.TW, Y0 = ty * P.TH;
-    const int X1 = min(X0 + P.TW, P.W) - 1, Y1 = min(Y0 + P.TH, P.H) - 1;
-    const int npix = P.TW * P.TH;
-    const int ppt = (npix + RT - 1) / RT;
-    for (int i = threadIdx.x; i < SPLAT_PPT * RT; i += RT) sAcc[i] = 0ull;
-    int px256[SPLAT_PPT], py256[SPLAT_PPT];
-    unsigned long long acc[SPLAT_PPT];
+    const int TWc = min(P.TW, P.W - X0), THc = min(P.TH, P.H - Y0); // tile clipped to the image
+    const int nbx = (P.TW + 7) >> 3, nblk = nbx * ((P.TH + 3) >> 2);
+    unsigned long long acc[SPLAT_SLOTS];
 #pragma unroll
-    for (int k = 0; k < SPLAT_PPT; ++k) {
-        const int p = threadIdx.x + k * RT;
-        px256[k] = (X0 + p % P.TW) * 256 + 128;
-        py256[k] = (Y0 + p / P.TW) * 256 + 128;
-        acc[k] = 0ull;
-    }
+    for (int k = 0; k < SPLAT_SLOTS; ++k) acc[k] = 0ull;
     for (uint32_t base = it.y; base < it.z; base += RT) {
         __syncthreads();
-        if (threadIdx.x == 0) {
-            nLarge = 0;
-            nSmall = 0;
-        }
-        __syncthreads();
-        const uint32_t r = base + threadIdx.x;
-        if (r < it.z) {
-            const uint4 R = rec[r];
+        const int nb = (int)min((uint32_t)RT, it.z - base);
+        if ((int)threadIdx.x < nb) {
+            const uint4 R = rec[base + threadIdx.x];
             const unsigned long long Wq = __float2ull_rn(__uint_as_float(R.w));
             sA[threadIdx.x] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)Wq);
             sWh[threadIdx.x] = (uint32_t)(Wq >> 32);
             int x0, x1, y0, y1;
             splat_box((int)R.x, (int)R.y, R.z, P.W, P.H, x0, x1, y0, y1);
-            x0 = max(x0, X0) - X0;
-            x1 = min(x1, X1) - X0;
-            y0 = max(y0, Y0) - Y0;
-            y1 = min(y1, Y1) - Y0;
-            if (x0 <= x1 && y0 <= y1) {
-                const int bw = x1 - x0 + 1, area = bw * (y1 - y0 + 1);
-                sBox[threadIdx.x] = (uint32_t)x0 | (uint32_t)x1 << 8 | (uint32_t)y0 << 16 | (uint32_t)y1 << 24;
-                if (area <= SMALL_MAX && bw <= 32)
-                    sSmall[atomicAdd(&nSmall, 1)] = (uint16_t)threadIdx.x;
-                else
-                    sLarge[atomicAdd(&nLarge, 1)] = (uint16_t)threadIdx.x;
-            }
+            x0 = max(x0 - X0, 0);
+            x1 = min(x1 - X0, TWc - 1);
+            y0 = max(y0 - Y0, 0);
+            y1 = min(y1 - Y0, THc - 1);
+            // an empty box touches no block: encode it with y0 = 255 > y1 = 0
+            sBox[threadIdx.x] = x0 <= x1 && y0 <= y1
+                                    ? (uint32_t)x0 | (uint32_t)x1 << 8 | (uint32_t)y0 << 16 | (uint32_t)y1 << 24
+                                    : 0x00FF0000u;
         }
         __syncthreads();
-        const int nl = nLarge, ns = nSmall;
-        // large records: every thread, its own pixels, register sums
-        if (ppt == 1) {
-            const int pxv = px256[0], pyv = py256[0];
-            unsigned long long a0 = acc[0];
-            for (int j = 0; j < nl; ++j) {
-                const int q = sLarge[j];
-                const int4 A = sA[q];
-                const unsigned long long W = ((unsigned long long)sWh[q] << 32) | (uint32_t)A.w;
+#pragma unroll
+        for (int k = 0; k < SPLAT_SLOTS; ++k) {
+            const int b = warp + k * (RT / 32);
+            if (b >= nblk) break; // warp-uniform
+            const int bx0 = (b % nbx) * 8, by0 = (b / nbx) * 4;
+            if (bx0 >= TWc || by0 >= THc) continue;
+            // records whose box touches this warp's block k
+            int cnt = 0;
+            for (int j0 = 0; j0 < nb; j0 += 32) {
+                const int j = j0 + lane;
+                bool touch = false;
+                if (j < nb) {
+                    const uint32_t bx = sBox[j];
+                    const int x0 = bx & 255, x1 = (bx >> 8) & 255, y0 = (bx >> 16) & 255, y1 = bx >> 24;
+                    touch = x0 <= bx0 + 7 && x1 >= bx0 && y0 <= by0 + 3 && y1 >= by0 && y0 <= y1;
+                }
+                const uint32_t m = __ballot_sync(0xffffffffu, touch);
+                if (touch) sList[warp][k][cnt + __popc(m & lt)] = (uint8_t)j;
+                cnt += __popc(m);
+            }
+            __syncwarp();
+            const int pxl = bx0 + (lane & 7), pyl = by0 + (lane >> 3);
+            const bool pv = pxl < TWc && pyl < THc;
+            const int pxv = (X0 + pxl) * 256 + 128, pyv = (Y0 + pyl) * 256 + 128;
+            unsigned long long a = acc[k];
+            for (int i = 0; i < cnt; ++i) {
+                const int j = sList[warp][k][i];
+                const int4 A = sA[j];
+                const unsigned long long W = ((unsigned long long)sWh[j] << 32) | (uint32_t)A.w;
                 unsigned long long c;
-                if (pixel_term(pxv - A.x, pyv - A.y, (uint32_t)A.z, W, K, c)) {
-                    a0 += c;
+                if (pixel_term(pxv - A.x, pyv - A.y, (uint32_t)A.z, W, K, c) && pv) {
+                    a += c;
                     ++hits;
                 }
             }
-            acc[0] = a0;
-        } else {
-            for (int j = 0; j < nl; ++j) {
-                const int q = sLarge[j];
-                const int4 A = sA[q];
-                const unsigned long long W = ((unsigned long long)sWh[q] << 32) | (uint32_t)A.w;
-#pragma unroll
-                for (int k = 0; k < SPLAT_PPT; ++k) {
-                    unsigned long long c;
-                    if (k < ppt && pixel_term(px256[k] - A.x, py256[k] - A.y, (uint32_t)A.z, W, K, c)) {
-                        acc[k] += c;
-                        ++hits;
-                    }
-                }
-            }
-        }
-        // small records: one warp each, lanes over the box pixels, shared accumulation
-        for (int j = warp; j < ns; j += RT / 32) {
-            const int q = sSmall[j];
-            const int4 A = sA[q];
-            const unsigned long long W = ((unsigned long long)sWh[q] << 32) | (uint32_t)A.w;
-            const uint32_t bx = sBox[q];
-            const int x0 = bx & 255, x1 = (bx >> 8) & 255, y0 = (bx >> 16) & 255, y1 = bx >> 24;
-            const int bw = x1 - x0 + 1;
-            const int rows = 32 / bw;
-            const int lx = x0 + sDivR[bw][lane];
-            const int l_row = sDivQ[bw][lane];
-            if (l_row < rows) {
-                const int dx = (X0 + lx) * 256 + 128 - A.x;
-                for (int ly = y0 + l_row; ly <= y1; ly += rows) {
-                    unsigned long long c;
-                    if (pixel_term(dx, (Y0 + ly) * 256 + 128 - A.y, (uint32_t)A.z, W, K, c)) {
-                        atomicAdd(&sAcc[ly * P.TW + lx], c);
-                        ++hits;
-                    }
-                }
-            }
+            acc[k] = a;
         }
     }
-    __syncthreads();
 #pragma unroll
-    for (int k = 0; k < SPLAT_PPT; ++k) {
-        const int p = threadIdx.x + k * RT;
-        if (k < ppt && p < npix) {
-            const unsigned long long v = acc[k] + sAcc[p];
-            const int gx = X0 + p % P.TW, gy = Y0 + p / P.TW;
-            if (v && gx < P.W && gy < P.H) atomicAdd(&img[(size_t)gy * P.W + gx], v);
-        }
+    for (int k = 0; k < SPLAT_SLOTS; ++k) {
+        const int b = warp + k * (RT / 32);
+        if (b >= nblk) break;
+        const int pxl = (b % nbx) * 8 + (lane & 7), pyl = (b / nbx) * 4 + (lane >> 3);
+        if (pxl < TWc && pyl < THc && acc[k]) atomicAdd(&img[(size_t)(Y0 + pyl) * P.W + (X0 + pxl)], acc[k]);
     }
     unsigned long long h64 = hits;
     for (int d = 16; d > 0; d >>= 1) h64 += __shfl_xor_sync(0xffffffffu, h64, d);
