@@ -120,6 +120,20 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def combine_ranks(ms: float, e2e_s: float, frames: int, world: int, device=None):
+    """Weak scaling over replicas: every rank rendered `frames` frames; the job takes as long as
+    the slowest rank.  Returns (max ms, max end-to-end seconds, frames of all ranks)."""
+    if world <= 1:
+        return ms, e2e_s, frames
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, e2e_s, float(frames)], dtype=torch.float64, device=device)
+    m = t.clone()
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(m[0]), float(m[1]), int(round(float(t[2])))
+
+
 def dist_info():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -220,6 +234,17 @@ def run_ours(a):
         lod_counts["points"] += s["points"]
         lod_counts["pixel_updates"] += s["pixel_updates"]
         lod_counts["nodes"] += s["nodes_selected"]
+    # visual equivalence (abstract: indistinguishable from a full rendering): LOD vs all points
+    vis = []
+    for cam in cams[:: max(1, nf // 8)]:
+        li, _ = r.render(tree, cam, par)
+        bi, _ = r.render_bruteforce(xyz, mass, h, cam, par)
+        d = (li.int() - bi.int()).abs().double()
+        mse = float((d * d).mean())
+        vis.append((float(d.max()), float(d.mean()), 10 * math.log10(255.0 ** 2 / mse) if mse > 0 else float("inf")))
+    visual = {"frames": len(vis), "max_abs_u8": max(v[0] for v in vis),
+              "mean_abs_u8": float(np.mean([v[1] for v in vis])), "psnr_db_mean": float(np.mean([v[2] for v in vis])),
+              "psnr_db_min": float(min(v[2] for v in vis))}
     info = tree.info()
     tree.free()
     assert r.status() == gblod.OK
@@ -276,16 +301,11 @@ def run_ours(a):
                "d2h_bytes_per_step": int(nf * W * H), "_s": e2e_s}
 
     # reduce over ranks: slowest time, all frames
-    if world > 1:
-        t = torch.tensor([tot_ms, e2e["_s"] if e2e else 0.0], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms, e2e_max = float(t[0]), float(t[1])
-        if e2e:
-            e2e["_s"] = e2e_max
-    frames_all = world * a.steps * nf
+    tot_ms, e2e_s, frames_all = combine_ranks(tot_ms, e2e["_s"] if e2e else 0.0, a.steps * nf, world, dev)
     value = frames_all / (tot_ms / 1e3)
     if e2e:
-        e2e["value"] = frames_all / e2e.pop("_s")
+        e2e.pop("_s")
+        e2e["value"] = frames_all / e2e_s
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -320,6 +340,7 @@ def run_ours(a):
                 "nodes_per_frame": lod_counts["nodes"] / nf,
                 "pixel_updates_per_frame": lod_counts["pixel_updates"] / nf},
         "build": {"ms": float(np.median(build_ms)), "particles_per_s": p.n / (np.median(build_ms) / 1e3)},
+        "visual_equivalence": visual,
         "all_points": brute,
         "clocks": ck,
         "e2e": e2e,

@@ -523,27 +523,22 @@ __global__ void k_fill_items(uint32_t ntiles, const uint32_t *tile_cnt, const ui
 // pixel blocks, one lane per pixel; block b belongs to warp b % 8 (up to SPLAT_SLOTS blocks per
 // warp).  Records are staged through shared memory in batches of RT; each warp first compacts,
 // by ballot, the records whose box touches each of its blocks, then evaluates only those for its
-// pixels and keeps the sums in registers (no atomics).  The table test (q S) >> 37 < 1024 is
-// evaluated exactly as q S < 2^47.  Each pixel's sum is added to the image once at the end.
+// pixels and keeps the sums in registers (no atomics).
+// Exact integer shortcuts of the per-pixel rule, all identities:
+//   (q S) >> 37 < 1024  <=>  q < QL = floor((2^47 - 1) / S) + 1     (one compare per miss)
+//   floor(Wq K / 2^16)   =   Wh K + floor(Wl K / 2^16),  Wq = Wh 2^16 + Wl, Wl < 2^16
+// Wh K goes to a 64-bit sum and floor(Wl K / 2^16) < 2^16 to a 32-bit one (at most ITEM = 2048
+// records per block keeps it below 2^27).  Each pixel's sum is added to the image once.
 constexpr int SPLAT_SLOTS = 4; // 8 warps x 4 blocks of 32 pixels: tiles up to 1024 pixels
-
-__device__ __forceinline__ bool pixel_term(int dx, int dy, uint32_t S, unsigned long long W, const int32_t *K,
-                                           unsigned long long &c)
-{
-    const unsigned long long q = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
-    const unsigned long long p = q * (unsigned long long)S;
-    if (p >= (1ull << 47)) return false;
-    c = (W * (unsigned long long)(uint32_t)K[p >> 37]) >> 16;
-    return true;
-}
+static_assert(ITEM <= (1u << 15), "32-bit partial sums need at most 2^15 records per item");
 
 __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
                                                        Proj P, unsigned long long *__restrict__ img,
                                                        FrameStatsDev *stats)
 {
     __shared__ int32_t K[1024];
-    __shared__ int4 sA[RT];                             // U, V, S, Wq low word
-    __shared__ uint32_t sWh[RT];                        // Wq high word
+    __shared__ int4 sA[RT];                             // U, V, S, Wh = Wq >> 16
+    __shared__ uint4 sB[RT];                            // QL low, QL high, Wl = Wq & 0xFFFF, unused
     __shared__ uint32_t sBox[RT];                       // tile-local box x0 | x1 << 8 | y0 << 16 | y1 << 24
     __shared__ uint8_t sList[RT / 32][SPLAT_SLOTS][RT]; // per warp and block: records touching it
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -556,16 +551,21 @@ __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__
     const int TWc = min(P.TW, P.W - X0), THc = min(P.TH, P.H - Y0); // tile clipped to the image
     const int nbx = (P.TW + 7) >> 3, nblk = nbx * ((P.TH + 3) >> 2);
     unsigned long long acc[SPLAT_SLOTS];
+    uint32_t acc_lo[SPLAT_SLOTS];
 #pragma unroll
-    for (int k = 0; k < SPLAT_SLOTS; ++k) acc[k] = 0ull;
+    for (int k = 0; k < SPLAT_SLOTS; ++k) {
+        acc[k] = 0ull;
+        acc_lo[k] = 0u;
+    }
     for (uint32_t base = it.y; base < it.z; base += RT) {
         __syncthreads();
         const int nb = (int)min((uint32_t)RT, it.z - base);
         if ((int)threadIdx.x < nb) {
             const uint4 R = rec[base + threadIdx.x];
             const unsigned long long Wq = __float2ull_rn(__uint_as_float(R.w));
-            sA[threadIdx.x] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)Wq);
-            sWh[threadIdx.x] = (uint32_t)(Wq >> 32);
+            const unsigned long long QL = 140737488355327ull / (unsigned long long)R.z + 1ull;
+            sA[threadIdx.x] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)(Wq >> 16));
+            sB[threadIdx.x] = make_uint4((uint32_t)QL, (uint32_t)(QL >> 32), (uint32_t)(Wq & 0xFFFFull), 0u);
             int x0, x1, y0, y1;
             splat_box((int)R.x, (int)R.y, R.z, P.W, P.H, x0, x1, y0, y1);
             x0 = max(x0 - X0, 0);
@@ -603,17 +603,25 @@ __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__
             const bool pv = pxl < TWc && pyl < THc;
             const int pxv = (X0 + pxl) * 256 + 128, pyv = (Y0 + pyl) * 256 + 128;
             unsigned long long a = acc[k];
+            uint32_t al = acc_lo[k];
+#pragma unroll 2
             for (int i = 0; i < cnt; ++i) {
                 const int j = sList[warp][k][i];
                 const int4 A = sA[j];
-                const unsigned long long W = ((unsigned long long)sWh[j] << 32) | (uint32_t)A.w;
-                unsigned long long c;
-                if (pixel_term(pxv - A.x, pyv - A.y, (uint32_t)A.z, W, K, c) && pv) {
-                    a += c;
+                const uint4 B = sB[j];
+                const int dx = pxv - A.x, dy = pyv - A.y;
+                const unsigned long long q = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
+                const unsigned long long QL = ((unsigned long long)B.y << 32) | B.x;
+                if (q < QL && pv) {
+                    const uint32_t idx = (uint32_t)((q * (unsigned long long)(uint32_t)A.z) >> 37);
+                    const uint32_t kv = (uint32_t)K[idx];
+                    a += (unsigned long long)(uint32_t)A.w * kv;
+                    al += (B.z * kv) >> 16;
                     ++hits;
                 }
             }
             acc[k] = a;
+            acc_lo[k] = al;
         }
     }
 #pragma unroll
@@ -621,7 +629,8 @@ __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__
         const int b = warp + k * (RT / 32);
         if (b >= nblk) break;
         const int pxl = (b % nbx) * 8 + (lane & 7), pyl = (b / nbx) * 4 + (lane >> 3);
-        if (pxl < TWc && pyl < THc && acc[k]) atomicAdd(&img[(size_t)(Y0 + pyl) * P.W + (X0 + pxl)], acc[k]);
+        const unsigned long long v = acc[k] + acc_lo[k];
+        if (pxl < TWc && pyl < THc && v) atomicAdd(&img[(size_t)(Y0 + pyl) * P.W + (X0 + pxl)], v);
     }
     unsigned long long h64 = hits;
     for (int d = 16; d > 0; d >>= 1) h64 += __shfl_xor_sync(0xffffffffu, h64, d);
