@@ -44,6 +44,7 @@ def args_():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-brute", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -269,6 +270,51 @@ def run_ours(a):
                      p50_ms=float(np.percentile(b_frames, 50)), p99_ms=float(np.percentile(b_frames, 99)),
                      splats_per_frame=b_counts["splats"] / nf, pixel_updates_per_frame=b_counts["pixel_updates"] / nf)
 
+    # batched views (one set of launches, no host waits) and its CUDA-graph replay
+    batched = None
+    if not a.no_batch:
+        bcams = cams[:: max(1, nf // 32)][:32]
+        tree = gblod.build_lod(xyz, mass, h, n_max=n_max, seed=1)
+        bviews = [(tree, c, torch.empty((H, W), dtype=torch.uint8, device=dev),
+                   torch.empty((H, W), dtype=torch.int64, device=dev)) for c in bcams]
+        par_b, _ = r.autotune(bviews, gblod.make_params(lambda_px=lam))
+        r.reserve_batch(bviews, par_b)
+
+        def ev_time(fn, reps):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        def singles():
+            for (t, c, im, ac) in bviews:
+                r.render(t, c, par_b, image=im, accum=ac)
+
+        ms_single = ev_time(singles, a.steps)
+        ms_batch = ev_time(lambda: r.render_batch(bviews, par_b), a.steps)
+        gs = torch.cuda.Stream()
+        gs.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(gs):
+            r.render_batch(bviews, par_b, stream=gs)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph, stream=gs):
+                r.render_batch(bviews, par_b, stream=gs)
+        torch.cuda.synchronize()
+        ms_graph = ev_time(graph.replay, a.steps)
+        batched = {"views": len(bviews), "resolution": f"{W}x{H}", "tile": [par_b.tile_w, par_b.tile_h],
+                   "views_per_s_one_at_a_time": len(bviews) / (ms_single / 1e3),
+                   "views_per_s_batch": len(bviews) / (ms_batch / 1e3),
+                   "views_per_s_graph_replay": len(bviews) / (ms_graph / 1e3),
+                   "status": int(r.status())}
+        del graph
+        tree.free()
+
     # end to end through the public API: pinned host inputs in, u8 frames out, every step
     e2e = None
     if not a.no_e2e:
@@ -342,6 +388,7 @@ def run_ours(a):
         "build": {"ms": float(np.median(build_ms)), "particles_per_s": p.n / (np.median(build_ms) / 1e3)},
         "visual_equivalence": visual,
         "all_points": brute,
+        "batched": batched,
         "clocks": ck,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -41,7 +41,8 @@ typedef enum {
     GBLOD_ERR_OOM = 3,           /* the allocator returned NULL */
     GBLOD_ERR_CUDA = 4,          /* a CUDA runtime call failed (message in gblod_last_error) */
     GBLOD_ERR_DEVICE_TIMEOUT = 5,/* a bounded device wait ran out */
-    GBLOD_ERR_NOT_IMPLEMENTED = 6
+    GBLOD_ERR_NOT_IMPLEMENTED = 6,
+    GBLOD_ERR_CAPACITY = 7       /* a batch needed more reserved scratch than it had; its images are invalid */
 } gblod_status;
 
 /* ----------------------------------------------------------------- memory */
@@ -158,7 +159,7 @@ typedef struct {
     int32_t kernel;       /* GBLOD_KERNEL_* */
     int32_t tone_auto;    /* 1: hi = image maximum, lo = 1e-4 hi */
     int32_t tile_w, tile_h; /* screen tile, 1..64 each, covering at most 32 blocks of 8 x 4
-                             pixels (ceil(w/8) ceil(h/4) <= 32; 0 = 16); any value gives the
+                             pixels (ceil(w/8) ceil(h/4) <= 32; 0 = 32); any value gives the
                              same image */
     uint64_t record_budget; /* most (tile, splat) records held at once (16 bytes each); 0 = 2^28,
                              capped at 2^31.  A frame needing more is binned and splatted in
@@ -208,6 +209,42 @@ gblod_status gblod_renderer_stats(gblod_renderer *r, void *stream, gblod_frame_s
 gblod_status gblod_renderer_last_selection(gblod_renderer *r, void *stream, uint32_t *h_nodes, uint64_t cap,
                                            uint64_t *count);
 
+/* ----------------------------------------------------------------- batched views */
+/* Many views in one set of launches (the paper's interactive use renders a stream of views; a
+ * serving system renders many viewers' views at once).  Each view has its own camera, resolution
+ * and octree (e.g. one octree per timestep).  Every view's images equal what gblod_render gives for
+ * it alone, bit for bit. */
+typedef struct {
+    const gblod_octree *octree; /* the view's octree */
+    gblod_camera camera;
+    uint8_t *d_image;           /* height x width uint8, or NULL */
+    uint64_t *d_accum;          /* height x width uint64 fixed-point image; required */
+} gblod_view;
+
+/* Sizes the renderer's batch scratch for batches no larger than `views` (node counts, tiles,
+ * pixels) with room for `record_capacity` (tile, splat) records (0 = 2^28, at most 2^32 - 1).
+ * Allocates; waits for `stream`. */
+gblod_status gblod_renderer_reserve_batch(gblod_renderer *r, const gblod_view *views, int32_t n_views,
+                                          const gblod_render_params *params, uint64_t record_capacity,
+                                          void *stream);
+
+/* Renders every view (R1-R4).  Enqueues work on `stream` and returns without waiting: no host
+ * synchronisation and no allocation happen inside, so the call can be recorded into a CUDA graph.
+ * Requires a prior gblod_renderer_reserve_batch covering this batch (GBLOD_ERR_INVALID_ARG
+ * otherwise).  A batch whose (tile, splat) records exceed the reserved capacity sets the sticky
+ * capacity status (gblod_renderer_status returns GBLOD_ERR_CAPACITY) and its images are invalid.
+ * The per-view constants are passed by value to a kernel at enqueue time, so the caller's arrays
+ * may be reused as soon as the call returns. */
+gblod_status gblod_render_batch(gblod_renderer *r, const gblod_view *views, int32_t n_views,
+                                const gblod_render_params *params, void *stream);
+
+/* Autotuner: renders the batch with each candidate screen tile (16x16, 32x16, 16x32, 32x32, 64x16)
+ * and keeps the fastest in params_inout->tile_w/tile_h (the image is the same for every tile);
+ * *best_ms gets its time.  Reserves as needed and waits for `stream`. */
+gblod_status gblod_autotune_tiles(gblod_renderer *r, const gblod_view *views, int32_t n_views,
+                                  gblod_render_params *params_inout, uint64_t record_capacity, void *stream,
+                                  double *best_ms);
+
 /* ----------------------------------------------------------------- fixed-scratch variant */
 /* Brute-force frame that allocates no memory.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- host applications that own the whole
@@ -222,8 +259,8 @@ gblod_status gblod_renderer_last_selection(gblod_renderer *r, void *stream, uint
  *     bytes, which every GPU that loads the library holds until the process exits;
  *   - the first call on a device also performs that device's set-up (resolves the array's device
  *     address and uploads the kernel table); make that first call before any stream capture;
- *   - frames are limited to GBLOD_NOALLOC_MAX_TILES screen tiles (e.g. 2048 x 2048 pixels with
- *     16 x 16 tiles; larger images are rejected with GBLOD_ERR_INVALID_ARG) and to
+ *   - frames are limited to GBLOD_NOALLOC_MAX_TILES screen tiles (e.g. 4096 x 4096 pixels with
+ *     the default 32 x 32 tiles; larger images are rejected with GBLOD_ERR_INVALID_ARG) and to
  *     GBLOD_NOALLOC_MAX_RECORDS (tile, splat) records (a frame that needs more returns
  *     GBLOD_ERR_RANGE before anything is splatted; d_accum is then left unspecified);
  *   - every call shares the one array, so calls that overlap on the GPU (on different streams, or
@@ -231,7 +268,7 @@ gblod_status gblod_renderer_last_selection(gblod_renderer *r, void *stream, uint
  *   - the fixed-point range checks are returned directly (GBLOD_ERR_RANGE) since there is no
  *     renderer object to hold a status word; the frame is still completed without the dropped
  *     splats.  The call waits once on `stream` mid-frame, like gblod_render_bruteforce. */
-#define GBLOD_NOALLOC_MAX_TILES 16384u
+#define GBLOD_NOALLOC_MAX_TILES 16384u /* e.g. 4096 x 4096 pixels with the default 32 x 32 tiles */
 #define GBLOD_NOALLOC_MAX_RECORDS 2097152u
 #define GBLOD_NOALLOC_SCRATCH_BYTES 34227456u /* 32.6 MiB */
 gblod_status gblod_render_bruteforce_noalloc(const float *d_xyz, const float *d_mass, const float *d_h, uint64_t n,

@@ -48,8 +48,8 @@ gblod_render_params check_params(const gblod_render_params *p)
     if (q.kernel != GBLOD_KERNEL_GAUSSIAN && q.kernel != GBLOD_KERNEL_CUBIC)
         fail(GBLOD_ERR_INVALID_ARG, "unknown kernel");
     if (std::isnan(q.lambda_px)) fail(GBLOD_ERR_INVALID_ARG, "lambda_px is NaN");
-    if (q.tile_w == 0) q.tile_w = 16;
-    if (q.tile_h == 0) q.tile_h = 16;
+    if (q.tile_w == 0) q.tile_w = 32;
+    if (q.tile_h == 0) q.tile_h = 32;
     if (q.tile_w < 1 || q.tile_h < 1 || q.tile_w > 64 || q.tile_h > 64 ||
         ((q.tile_w + 7) / 8) * ((q.tile_h + 3) / 4) > 32)
         fail(GBLOD_ERR_INVALID_ARG, "tile must be 1..64 x 1..64 and cover at most 32 blocks of 8 x 4 pixels");
@@ -191,6 +191,71 @@ gblod_status gblod_render_bruteforce_noalloc(const float *d_xyz, const float *d_
     return st != GBLOD_OK ? st : out;
 }
 
+gblod_status gblod_renderer_reserve_batch(gblod_renderer *r, const gblod_view *views, int32_t n_views,
+                                          const gblod_render_params *params, uint64_t record_capacity, void *stream)
+{
+    return guarded([&] {
+        if (!r || !views || n_views < 1) fail(GBLOD_ERR_INVALID_ARG, "renderer and at least one view needed");
+        const gblod_render_params p = check_params(params);
+        for (int i = 0; i < n_views; ++i) check_camera(&views[i].camera);
+        reserve_batch(r, views, n_views, p, record_capacity, (cudaStream_t)stream);
+    });
+}
+
+gblod_status gblod_render_batch(gblod_renderer *r, const gblod_view *views, int32_t n_views,
+                                const gblod_render_params *params, void *stream)
+{
+    return guarded([&] {
+        if (!r || !views || n_views < 1) fail(GBLOD_ERR_INVALID_ARG, "renderer and at least one view needed");
+        const gblod_render_params p = check_params(params);
+        for (int i = 0; i < n_views; ++i) check_camera(&views[i].camera);
+        render_batch(r, views, n_views, p, (cudaStream_t)stream);
+    });
+}
+
+gblod_status gblod_autotune_tiles(gblod_renderer *r, const gblod_view *views, int32_t n_views,
+                                  gblod_render_params *params_inout, uint64_t record_capacity, void *stream,
+                                  double *best_ms)
+{
+    return guarded([&] {
+        if (!r || !views || n_views < 1 || !params_inout) fail(GBLOD_ERR_INVALID_ARG, "bad autotune arguments");
+        gblod_render_params p = check_params(params_inout);
+        for (int i = 0; i < n_views; ++i) check_camera(&views[i].camera);
+        static const int cand[][2] = {{16, 16}, {32, 16}, {16, 32}, {32, 32}, {64, 16}};
+        cudaStream_t s = (cudaStream_t)stream;
+        cudaEvent_t e0, e1;
+        GB_CUDA(cudaEventCreate(&e0));
+        GB_CUDA(cudaEventCreate(&e1));
+        double best = -1.0;
+        int bw = p.tile_w, bh = p.tile_h;
+        for (const auto &c : cand) {
+            p.tile_w = c[0];
+            p.tile_h = c[1];
+            reserve_batch(r, views, n_views, p, record_capacity, s);
+            render_batch(r, views, n_views, p, s); // warm-up
+            GB_CUDA(cudaEventRecord(e0, s));
+            for (int k = 0; k < 3; ++k) render_batch(r, views, n_views, p, s);
+            GB_CUDA(cudaEventRecord(e1, s));
+            GB_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            GB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (best < 0.0 || ms / 3.0 < best) {
+                best = ms / 3.0;
+                bw = c[0];
+                bh = c[1];
+            }
+        }
+        (void)cudaEventDestroy(e0);
+        (void)cudaEventDestroy(e1);
+        params_inout->tile_w = bw;
+        params_inout->tile_h = bh;
+        p.tile_w = bw;
+        p.tile_h = bh;
+        reserve_batch(r, views, n_views, p, record_capacity, s);
+        if (best_ms) *best_ms = best;
+    });
+}
+
 gblod_status gblod_renderer_status(gblod_renderer *r, void *stream, int reset)
 {
     gblod_status out = GBLOD_OK;
@@ -207,6 +272,8 @@ gblod_status gblod_renderer_status(gblod_renderer *r, void *stream, int reset)
         if (reset) GB_CUDA(cudaMemsetAsync(r->status, 0, 4, s));
         if (bits & 2u)
             out = GBLOD_ERR_DEVICE_TIMEOUT;
+        else if (bits & 4u)
+            out = GBLOD_ERR_CAPACITY;
         else if (bits & 1u)
             out = GBLOD_ERR_RANGE;
         if (reset) GB_CUDA(cudaStreamSynchronize(s));

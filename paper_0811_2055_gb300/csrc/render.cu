@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -17,6 +18,8 @@
 #include "render.cuh"
 
 namespace gb {
+
+void check_image(const gblod_camera &c);
 
 // integer kernel tables (Gaussian, cubic), filled once per device
 __device__ int32_t g_ktab[2][1024];
@@ -98,8 +101,8 @@ Proj make_proj(const gblod_camera &c, const gblod_render_params &rp)
     P.Hf = (float)c.height;
     P.W = c.width;
     P.H = c.height;
-    P.TW = rp.tile_w > 0 ? rp.tile_w : 16;
-    P.TH = rp.tile_h > 0 ? rp.tile_h : 16;
+    P.TW = rp.tile_w > 0 ? rp.tile_w : 32;
+    P.TH = rp.tile_h > 0 ? rp.tile_h : 32;
     P.tiles_x = (P.W + P.TW - 1) / P.TW;
     P.tiles_y = (P.H + P.TH - 1) / P.TH;
     P.kernel = cubic ? 1 : 0;
@@ -532,21 +535,22 @@ __global__ void k_fill_items(uint32_t ntiles, const uint32_t *tile_cnt, const ui
 constexpr int SPLAT_SLOTS = 4; // 8 warps x 4 blocks of 32 pixels: tiles up to 1024 pixels
 static_assert(ITEM <= (1u << 15), "32-bit partial sums need at most 2^15 records per item");
 
-__global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
-                                                       Proj P, unsigned long long *__restrict__ img,
-                                                       FrameStatsDev *stats)
+struct SplatSmem {
+    int32_t K[1024];
+    int4 A[RT];                             // U, V, S, Wh = Wq >> 16
+    uint4 B[RT];                            // QL low, QL high, Wl = Wq & 0xFFFF, unused
+    uint32_t box[RT];                       // tile-local box x0 | x1 << 8 | y0 << 16 | y1 << 24
+    uint8_t list[RT / 32][SPLAT_SLOTS][RT]; // per warp and block: records touching it
+};
+
+// Splats records [it.y, it.z) of tile `tile` (index inside the view) of view P into img.
+__device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const uint4 it, const uint32_t tile,
+                                           const Proj &P, unsigned long long *__restrict__ img, SplatSmem &sm,
+                                           unsigned &hits)
 {
-    __shared__ int32_t K[1024];
-    __shared__ int4 sA[RT];                             // U, V, S, Wh = Wq >> 16
-    __shared__ uint4 sB[RT];                            // QL low, QL high, Wl = Wq & 0xFFFF, unused
-    __shared__ uint32_t sBox[RT];                       // tile-local box x0 | x1 << 8 | y0 << 16 | y1 << 24
-    __shared__ uint8_t sList[RT / 32][SPLAT_SLOTS][RT]; // per warp and block: records touching it
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = gbd::lanemask_lt();
-    unsigned hits = 0;
-    for (int i = threadIdx.x; i < 1024; i += RT) K[i] = g_ktab[P.kernel][i];
-    const uint4 it = items[blockIdx.x];
-    const int tx = (int)(it.x % (uint32_t)P.tiles_x), ty = (int)(it.x / (uint32_t)P.tiles_x);
+    const int tx = (int)(tile % (uint32_t)P.tiles_x), ty = (int)(tile / (uint32_t)P.tiles_x);
     const int X0 = tx * P.TW, Y0 = ty * P.TH;
     const int TWc = min(P.TW, P.W - X0), THc = min(P.TH, P.H - Y0); // tile clipped to the image
     const int nbx = (P.TW + 7) >> 3, nblk = nbx * ((P.TH + 3) >> 2);
@@ -564,8 +568,8 @@ __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__
             const uint4 R = rec[base + threadIdx.x];
             const unsigned long long Wq = __float2ull_rn(__uint_as_float(R.w));
             const unsigned long long QL = 140737488355327ull / (unsigned long long)R.z + 1ull;
-            sA[threadIdx.x] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)(Wq >> 16));
-            sB[threadIdx.x] = make_uint4((uint32_t)QL, (uint32_t)(QL >> 32), (uint32_t)(Wq & 0xFFFFull), 0u);
+            sm.A[threadIdx.x] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)(Wq >> 16));
+            sm.B[threadIdx.x] = make_uint4((uint32_t)QL, (uint32_t)(QL >> 32), (uint32_t)(Wq & 0xFFFFull), 0u);
             int x0, x1, y0, y1;
             splat_box((int)R.x, (int)R.y, R.z, P.W, P.H, x0, x1, y0, y1);
             x0 = max(x0 - X0, 0);
@@ -573,9 +577,9 @@ __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__
             y0 = max(y0 - Y0, 0);
             y1 = min(y1 - Y0, THc - 1);
             // an empty box touches no block: encode it with y0 = 255 > y1 = 0
-            sBox[threadIdx.x] = x0 <= x1 && y0 <= y1
-                                    ? (uint32_t)x0 | (uint32_t)x1 << 8 | (uint32_t)y0 << 16 | (uint32_t)y1 << 24
-                                    : 0x00FF0000u;
+            sm.box[threadIdx.x] = x0 <= x1 && y0 <= y1
+                                      ? (uint32_t)x0 | (uint32_t)x1 << 8 | (uint32_t)y0 << 16 | (uint32_t)y1 << 24
+                                      : 0x00FF0000u;
         }
         __syncthreads();
 #pragma unroll
@@ -590,12 +594,12 @@ __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__
                 const int j = j0 + lane;
                 bool touch = false;
                 if (j < nb) {
-                    const uint32_t bx = sBox[j];
+                    const uint32_t bx = sm.box[j];
                     const int x0 = bx & 255, x1 = (bx >> 8) & 255, y0 = (bx >> 16) & 255, y1 = bx >> 24;
                     touch = x0 <= bx0 + 7 && x1 >= bx0 && y0 <= by0 + 3 && y1 >= by0 && y0 <= y1;
                 }
                 const uint32_t m = __ballot_sync(0xffffffffu, touch);
-                if (touch) sList[warp][k][cnt + __popc(m & lt)] = (uint8_t)j;
+                if (touch) sm.list[warp][k][cnt + __popc(m & lt)] = (uint8_t)j;
                 cnt += __popc(m);
             }
             __syncwarp();
@@ -606,15 +610,15 @@ __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__
             uint32_t al = acc_lo[k];
 #pragma unroll 2
             for (int i = 0; i < cnt; ++i) {
-                const int j = sList[warp][k][i];
-                const int4 A = sA[j];
-                const uint4 B = sB[j];
+                const int j = sm.list[warp][k][i];
+                const int4 A = sm.A[j];
+                const uint4 B = sm.B[j];
                 const int dx = pxv - A.x, dy = pyv - A.y;
                 const unsigned long long q = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
                 const unsigned long long QL = ((unsigned long long)B.y << 32) | B.x;
                 if (q < QL && pv) {
                     const uint32_t idx = (uint32_t)((q * (unsigned long long)(uint32_t)A.z) >> 37);
-                    const uint32_t kv = (uint32_t)K[idx];
+                    const uint32_t kv = (uint32_t)sm.K[idx];
                     a += (unsigned long long)(uint32_t)A.w * kv;
                     al += (B.z * kv) >> 16;
                     ++hits;
@@ -632,12 +636,28 @@ __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__
         const unsigned long long v = acc[k] + acc_lo[k];
         if (pxl < TWc && pyl < THc && v) atomicAdd(&img[(size_t)(Y0 + pyl) * P.W + (X0 + pxl)], v);
     }
+}
+
+__device__ __forceinline__ void count_hits(unsigned hits, FrameStatsDev *stats)
+{
     unsigned long long h64 = hits;
     for (int d = 16; d > 0; d >>= 1) h64 += __shfl_xor_sync(0xffffffffu, h64, d);
-    if (lane == 0 && h64) {
+    if ((threadIdx.x & 31) == 0 && h64) {
         atomicAdd(&stats->pixel_updates, h64);
         atomicAdd(&stats->pixel_updates_total, h64);
     }
+}
+
+__global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
+                                                       Proj P, unsigned long long *__restrict__ img,
+                                                       FrameStatsDev *stats)
+{
+    __shared__ SplatSmem sm;
+    for (int i = threadIdx.x; i < 1024; i += RT) sm.K[i] = g_ktab[P.kernel][i];
+    unsigned hits = 0;
+    const uint4 it = items[blockIdx.x];
+    splat_item(rec, it, it.x, P, img, sm, hits);
+    count_hits(hits, stats);
 }
 
 // ------------------------------------------------------------------ R4
@@ -828,6 +848,489 @@ void frame_common(gblod_renderer *r, const Src &src, const Proj &P, const gblod_
     }
 }
 
+
+// ------------------------------------------------------------------ batched views (no host waits)
+// Many views -- each with its own camera, resolution and octree -- rendered by one set of
+// launches: R1 walks (view, node) pairs, the points of all selected nodes of all views form one
+// flat index space, screen tiles of all views one global tile space, and persistent kernels read
+// every data-dependent count from device memory.  Nothing waits on the host, so the sequence can
+// be captured in a CUDA graph.  Scratch has a reserved capacity; a batch that needs more sets the
+// sticky capacity bit of the renderer's status instead of growing it.
+constexpr unsigned ST_CAPACITY = 4u;
+constexpr int VIEWS_PER_CHUNK = 40;
+
+struct ViewDev {
+    Proj P;
+    Frustum F;
+    const gblod_node *nodes;
+    const float4 *pts4;
+    const float *hs;
+    unsigned long long *accum;
+    uint8_t *image;
+    unsigned long long pix_base;
+    uint32_t tile_base, n_nodes;
+    double lo_acc, hi_acc; // fixed tone range in accumulator units (unused when automatic)
+};
+
+struct ViewChunk {
+    int first, n;
+    ViewDev v[VIEWS_PER_CHUNK];
+};
+static_assert(sizeof(ViewChunk) < 30000, "kernel parameter block too large");
+
+__global__ void k_set_views(ViewChunk c, ViewDev *dst)
+{
+    for (int i = threadIdx.x; i < c.n; i += blockDim.x) dst[c.first + i] = c.v[i];
+}
+
+__global__ void k_bzero(const ViewDev *__restrict__ views, int n, unsigned long long total)
+{
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (views[mid].pix_base <= e) lo = mid; else hi = mid;
+        }
+        views[lo].accum[e - views[lo].pix_base] = 0ull;
+    }
+}
+
+__global__ void k_bselect_init(const ViewDev *__restrict__ views, int n, unsigned long long *front, uint32_t *cnt)
+{
+    for (int v = threadIdx.x; v < n; v += blockDim.x)
+        if (views[v].n_nodes) front[atomicAdd(cnt, 1u)] = (unsigned long long)v << 32;
+}
+
+__global__ void __launch_bounds__(RT) k_bselect_level(const ViewDev *__restrict__ views,
+                                                      const unsigned long long *__restrict__ fin, const uint32_t *nin,
+                                                      unsigned long long *__restrict__ fout, uint32_t *nout,
+                                                      unsigned long long *__restrict__ sel, uint32_t *nsel)
+{
+    const uint32_t n = *nin;
+    const uint32_t lt = gbd::lanemask_lt();
+    const int lane = threadIdx.x & 31;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        int cls = 0;
+        unsigned long long ent = 0;
+        uint32_t ccount = 0, cfirst = 0;
+        if (i < n) {
+            ent = fin[i];
+            const int v = (int)(ent >> 32);
+            const gblod_node g = views[v].nodes[(uint32_t)ent];
+            cls = classify(g, views[v].F);
+            ccount = g.child_count;
+            cfirst = g.child_first;
+        }
+        const uint32_t em = __ballot_sync(0xffffffffu, cls == 1);
+        if (em) {
+            const int leader = __ffs(em) - 1;
+            uint32_t b = 0;
+            if (lane == leader) b = atomicAdd(nsel, (uint32_t)__popc(em));
+            b = __shfl_sync(0xffffffffu, b, leader);
+            if (cls == 1) sel[b + __popc(em & lt)] = ent;
+        }
+        uint32_t want = cls == 2 ? ccount : 0u, incl = want;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+            uint32_t b = 0;
+            if (lane == 31) b = atomicAdd(nout, total);
+            b = __shfl_sync(0xffffffffu, b, 31);
+            const uint32_t at = b + incl - want;
+            const unsigned long long hiv = ent & 0xFFFFFFFF00000000ull;
+            for (uint32_t k = 0; k < want; ++k) fout[at + k] = hiv | (cfirst + k);
+        }
+    }
+}
+
+__global__ void k_bsel_counts(const ViewDev *__restrict__ views, const unsigned long long *__restrict__ sel,
+                              const uint32_t *nsel, uint32_t cap, unsigned long long *counts)
+{
+    const uint32_t n = *nsel;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+        unsigned long long c = 0;
+        if (i < n) {
+            const unsigned long long e = sel[i];
+            c = views[e >> 32].nodes[(uint32_t)e].point_count;
+        }
+        counts[i] = c;
+    }
+}
+
+__global__ void k_bsel_base(const ViewDev *__restrict__ views, const unsigned long long *__restrict__ sel,
+                            const uint32_t *nsel, const unsigned long long *__restrict__ pfx, long long *base,
+                            FrameStatsDev *stats)
+{
+    const uint32_t n = *nsel;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long e = sel[i];
+        base[i] = (long long)views[e >> 32].nodes[(uint32_t)e].point_first - (long long)pfx[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) stats->nodes_selected = n;
+}
+
+struct SrcBatch {
+    const ViewDev *views;
+    const unsigned long long *sel;
+    const unsigned long long *pfx;
+    const long long *base;
+    const uint32_t *nsel;
+    const unsigned long long *total;
+};
+
+__device__ __forceinline__ void bsrc_range(const SrcBatch &s, unsigned long long a, unsigned long long b,
+                                           uint32_t &j0, uint32_t &j1)
+{
+    __shared__ uint32_t sj[2];
+    if (threadIdx.x < 2) {
+        const unsigned long long v = threadIdx.x == 0 ? a : b - 1;
+        uint32_t lo = 0, hi = *s.nsel;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s.pfx[mid] <= v) lo = mid; else hi = mid;
+        }
+        sj[threadIdx.x] = lo;
+    }
+    __syncthreads();
+    j0 = sj[0];
+    j1 = sj[1];
+    __syncthreads();
+}
+
+// point e of the flat space: its view and its data
+__device__ __forceinline__ int bsrc_load(const SrcBatch &s, unsigned long long e, uint32_t j0, uint32_t j1, float &x,
+                                         float &y, float &z, float &w, float &h)
+{
+    uint32_t lo = j0, hi = j1 + 1;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s.pfx[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int v = (int)(s.sel[lo] >> 32);
+    const unsigned long long p = (unsigned long long)((long long)e + s.base[lo]);
+    const float4 q = s.views[v].pts4[p];
+    x = q.x; y = q.y; z = q.z; w = q.w;
+    h = s.views[v].hs[p];
+    return v;
+}
+
+template <bool SCATTER>
+__global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restrict__ tile_cnt,
+                                                 uint32_t *__restrict__ cursor, uint4 *__restrict__ rec,
+                                                 unsigned long long rec_cap, unsigned *status, FrameStatsDev *stats)
+{
+    const unsigned long long total = *src.total;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = gbd::lanemask_lt();
+    unsigned long long splats = 0, pairs = 0;
+    for (unsigned long long a = (unsigned long long)blockIdx.x * CHUNK; a < total;
+         a += (unsigned long long)gridDim.x * CHUNK) {
+        const unsigned long long b = min(total, a + CHUNK);
+        uint32_t j0, j1;
+        bsrc_range(src, a, b, j0, j1);
+        for (unsigned long long e0 = a; e0 < b; e0 += RT) {
+            const unsigned long long e = e0 + threadIdx.x;
+            int res = 0, v = 0;
+            Splat s;
+            if (e < b) {
+                float x, y, z, w, h;
+                v = bsrc_load(src, e, j0, j1, x, y, z, w, h);
+                res = project(src.views[v].P, x, y, z, w, h, s);
+            }
+            if (!SCATTER) {
+                if (__any_sync(0xffffffffu, res < 0) && lane == 0) atomicOr(status, ST_RANGE);
+                unsigned long long wq = res == 1 ? __float2ull_rn(s.Wf) : 0ull;
+                for (int d = 16; d > 0; d >>= 1) wq += __shfl_xor_sync(0xffffffffu, wq, d);
+                if (lane == 0 && wq) {
+                    const unsigned long long old = atomicAdd(&stats->amp_lo, wq);
+                    if (old + wq < old) atomicAdd(&stats->amp_hi, 1ull);
+                }
+            }
+            if (res == 1) {
+                const Proj &P = src.views[v].P;
+                const uint32_t tb = src.views[v].tile_base;
+                if (!SCATTER) ++splats;
+                int x0, x1, y0, y1;
+                splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
+                if (x0 <= x1 && y0 <= y1) {
+                    const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
+                    if (!SCATTER) pairs += (unsigned long long)(tx1 - tx0 + 1) * (unsigned long long)(ty1 - ty0 + 1);
+                    const uint4 r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
+                    for (int ty = ty0; ty <= ty1; ++ty)
+                        for (int tx = tx0; tx <= tx1; ++tx) {
+                            const uint32_t t = tb + (uint32_t)(ty * P.tiles_x + tx);
+                            const uint32_t mask = __activemask();
+                            const uint32_t peers = __match_any_sync(mask, t);
+                            const int leader = __ffs(peers) - 1;
+                            if (!SCATTER) {
+                                if (lane == leader) atomicAdd(&tile_cnt[t], (uint32_t)__popc(peers));
+                            } else {
+                                uint32_t base = 0;
+                                if (lane == leader) base = atomicAdd(&cursor[t], (uint32_t)__popc(peers));
+                                base = __shfl_sync(peers, base, leader);
+                                const unsigned long long pos = (unsigned long long)base + __popc(peers & lt);
+                                if (pos < rec_cap) rec[pos] = r;
+                            }
+                        }
+                }
+            }
+        }
+    }
+    if (!SCATTER) {
+        for (int d = 16; d > 0; d >>= 1) {
+            splats += __shfl_xor_sync(0xffffffffu, splats, d);
+            pairs += __shfl_xor_sync(0xffffffffu, pairs, d);
+        }
+        if (lane == 0 && splats) atomicAdd(&stats->splats, splats);
+        if (lane == 0 && pairs) atomicAdd(&stats->pairs, pairs);
+    }
+}
+
+// items of every tile of every view; a tile's view comes from the tile bases
+__global__ void k_bfill_items(uint32_t ntiles, const ViewDev *__restrict__ views, int nviews,
+                              const uint32_t *tile_cnt, const uint32_t *tile_off, const uint32_t *item_off,
+                              uint4 *items, uint32_t items_cap, unsigned long long rec_cap,
+                              const FrameStatsDev *stats, unsigned *status)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0 && (stats->pairs > rec_cap || item_off[ntiles] > items_cap)) atomicOr(status, ST_CAPACITY);
+    if (t >= ntiles) return;
+    int lo = 0, hi = nviews;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (views[mid].tile_base <= t) lo = mid; else hi = mid;
+    }
+    const uint32_t c = tile_cnt[t], o = tile_off[t], local = t - views[lo].tile_base;
+    uint32_t k = item_off[t];
+    for (uint32_t s = 0; s < c && k < items_cap; s += ITEM, ++k) {
+        const uint32_t b = o + s, e = o + min(c, s + ITEM);
+        // records beyond the capacity were never written: clip (the batch is flagged)
+        const uint32_t bc = (uint32_t)min((unsigned long long)b, rec_cap), ec = (uint32_t)min((unsigned long long)e, rec_cap);
+        items[k] = make_uint4(local, bc, ec, (uint32_t)lo);
+    }
+}
+
+__global__ void __launch_bounds__(RT, 4) k_bsplat(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
+                                                  const uint32_t *nitems_p, uint32_t items_cap,
+                                                  const ViewDev *__restrict__ views, FrameStatsDev *stats)
+{
+    __shared__ SplatSmem sm;
+    __shared__ Proj sP;
+    int kernel_loaded = -1;
+    unsigned hits = 0;
+    const uint32_t nitems = min(*nitems_p, items_cap);
+    for (uint32_t i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const uint4 it = items[i];
+        __syncthreads();
+        if (threadIdx.x == 0) sP = views[it.w].P;
+        __syncthreads();
+        const Proj P = sP;
+        if (P.kernel != kernel_loaded) {
+            for (int j = threadIdx.x; j < 1024; j += RT) sm.K[j] = g_ktab[P.kernel][j];
+            kernel_loaded = P.kernel;
+        }
+        splat_item(rec, it, it.x, P, views[it.w].accum, sm, hits);
+    }
+    count_hits(hits, stats);
+}
+
+__global__ void k_bmax(const ViewDev *__restrict__ views, int n, unsigned long long total, unsigned long long *maxv)
+{
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (views[mid].pix_base <= e) lo = mid; else hi = mid;
+        }
+        const unsigned long long a = views[lo].accum[e - views[lo].pix_base];
+        if (a) atomicMax(&maxv[lo], a);
+    }
+}
+
+__global__ void k_btonemap(const ViewDev *__restrict__ views, int n, unsigned long long total,
+                           const unsigned long long *maxv, int auto_range)
+{
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        int lo_v = 0, hi_v = n;
+        while (hi_v - lo_v > 1) {
+            const int mid = (lo_v + hi_v) >> 1;
+            if (views[mid].pix_base <= e) lo_v = mid; else hi_v = mid;
+        }
+        const ViewDev &V = views[lo_v];
+        if (!V.image) continue;
+        double hi = V.hi_acc, lo = V.lo_acc;
+        if (auto_range) {
+            hi = (double)maxv[lo_v];
+            lo = hi * 1e-4;
+        }
+        const unsigned long long local = e - V.pix_base;
+        const unsigned long long a = V.accum[local];
+        uint8_t o = 0;
+        if (hi > 0.0 && lo > 0.0 && hi > lo && (double)a > lo) {
+            const float l2lo = (float)log2(lo), scale = (float)(255.0 / log2(hi / lo));
+            const float t = rintf((log2f((float)a) - l2lo) * scale);
+            o = (uint8_t)(t > 255.0f ? 255.0f : (t < 0.0f ? 0.0f : t));
+        }
+        V.image[local] = o;
+    }
+}
+
+struct BatchPlan {
+    std::vector<ViewDev> host;
+    uint32_t ntiles = 0, max_levels = 0;
+    unsigned long long npix = 0;
+    uint64_t nodes = 0;
+};
+
+BatchPlan plan_batch(const gblod_view *views, int n, const gblod_render_params &rp)
+{
+    BatchPlan b;
+    b.host.resize(n);
+    for (int v = 0; v < n; ++v) {
+        const gblod_view &V = views[v];
+        if (!V.octree) fail(GBLOD_ERR_INVALID_ARG, "batch view has no octree");
+        if (!V.d_accum) fail(GBLOD_ERR_INVALID_ARG, "batch views need d_accum");
+        check_image(V.camera);
+        ViewDev &d = b.host[v];
+        std::memset(&d, 0, sizeof(d));
+        d.P = make_proj(V.camera, rp);
+        d.F = make_frustum(V.camera, rp, V.octree);
+        d.nodes = V.octree->nodes;
+        d.pts4 = V.octree->pts4;
+        d.hs = V.octree->hs;
+        d.accum = reinterpret_cast<unsigned long long *>(V.d_accum);
+        d.image = V.d_image;
+        d.pix_base = b.npix;
+        d.tile_base = b.ntiles;
+        d.n_nodes = (uint32_t)V.octree->n_nodes;
+        d.lo_acc = std::ldexp(rp.tone_lo, 32);
+        d.hi_acc = std::ldexp(rp.tone_hi, 32);
+        const unsigned long long tiles = (unsigned long long)d.P.tiles_x * d.P.tiles_y;
+        if ((unsigned long long)b.ntiles + tiles > 0x7FFFFFFFull) fail(GBLOD_ERR_INVALID_ARG, "too many tiles in batch");
+        b.ntiles += (uint32_t)tiles;
+        b.npix += (unsigned long long)d.P.W * d.P.H;
+        b.nodes += V.octree->n_nodes;
+        b.max_levels = std::max<uint32_t>(b.max_levels, (uint32_t)V.octree->depth_max + 1);
+    }
+    if (b.nodes >= 0xFFFFFFFFull) fail(GBLOD_ERR_INVALID_ARG, "too many nodes in batch");
+    return b;
+}
+
+} // namespace
+
+void reserve_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod_render_params &rp,
+                   uint64_t record_capacity, cudaStream_t s)
+{
+    if (n < 1) fail(GBLOD_ERR_INVALID_ARG, "batch needs at least one view");
+    const BatchPlan b = plan_batch(views, n, rp);
+    const Allocator &A = r->A;
+    const uint64_t rec_cap = record_capacity ? record_capacity : RECORD_BUDGET_DEFAULT;
+    if (rec_cap > 0xFFFFFFFFull) fail(GBLOD_ERR_INVALID_ARG, "record capacity must stay below 2^32");
+    r->b_views.ensure(A, (size_t)n * sizeof(ViewDev), s);
+    r->b_frontA.ensure(A, b.nodes + 1, s);
+    r->b_frontB.ensure(A, b.nodes + 1, s);
+    r->b_sel.ensure(A, b.nodes + 1, s);
+    r->b_counts.ensure(A, b.nodes + 1, s);
+    r->b_pfx.ensure(A, b.nodes + 2, s);
+    r->b_base.ensure(A, b.nodes + 1, s);
+    r->lvl_cnt.ensure(A, b.max_levels + 2, s);
+    r->tile_cnt.ensure(A, b.ntiles, s);
+    r->tile_off.ensure(A, b.ntiles + 1, s);
+    r->tile_cur.ensure(A, b.ntiles, s);
+    r->item_cnt.ensure(A, b.ntiles, s);
+    r->item_off.ensure(A, b.ntiles + 1, s);
+    r->records.ensure(A, rec_cap, s);
+    r->items.ensure(A, b.ntiles + rec_cap / ITEM + 1, s);
+    r->maxv.ensure(A, n, s);
+    // scan temp for the largest scans of this batch
+    scan_exclusive_u64(A, r->scan, reinterpret_cast<const uint64_t *>(r->b_counts.p),
+                       reinterpret_cast<uint64_t *>(r->b_pfx.p), b.nodes + 1, nullptr, s);
+    scan_exclusive_u32(A, r->scan, r->tile_cnt.p, r->tile_off.p, b.ntiles, nullptr, s);
+    r->b_rec_cap = rec_cap;
+    GB_CUDA(cudaStreamSynchronize(s));
+}
+
+void render_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod_render_params &rp, cudaStream_t s)
+{
+    if (n < 1) fail(GBLOD_ERR_INVALID_ARG, "batch needs at least one view");
+    BatchPlan b = plan_batch(views, n, rp);
+    const Allocator &A = r->A;
+    // scratch must have been reserved (no allocation here, so the call can be graph-captured)
+    const uint64_t items_cap = b.ntiles + r->b_rec_cap / ITEM + 1;
+    if (r->b_views.cap < (size_t)n * sizeof(ViewDev) || r->b_frontA.cap < b.nodes + 1 || r->b_sel.cap < b.nodes + 1 ||
+        r->b_pfx.cap < b.nodes + 2 || r->lvl_cnt.cap < b.max_levels + 2 || r->tile_cnt.cap < b.ntiles ||
+        r->tile_off.cap < b.ntiles + 1 || r->item_off.cap < b.ntiles + 1 || r->records.cap < r->b_rec_cap ||
+        r->items.cap < items_cap || r->maxv.cap < (size_t)n || r->b_rec_cap == 0)
+        fail(GBLOD_ERR_INVALID_ARG, "gblod_render_batch: call gblod_renderer_reserve_batch for this batch first");
+    r->last_stream = s;
+    r->last_was_lod = false;
+    ViewDev *dv = reinterpret_cast<ViewDev *>(r->b_views.p);
+    for (int c0 = 0; c0 < n; c0 += VIEWS_PER_CHUNK) {
+        ViewChunk ch;
+        ch.first = c0;
+        ch.n = std::min(VIEWS_PER_CHUNK, n - c0);
+        for (int i = 0; i < ch.n; ++i) ch.v[i] = b.host[c0 + i];
+        launch(GBLOD_K_RENDER_OTHER, k_set_views, dim3(1), dim3(64), 0, s, ch, dv);
+    }
+    const unsigned G = (unsigned)persistent_blocks(4);
+    GB_CUDA(cudaMemsetAsync(r->stats, 0, offsetof(FrameStatsDev, pixel_updates_total), s));
+    GB_CUDA(cudaMemsetAsync(r->lvl_cnt.p, 0, (size_t)(b.max_levels + 2) * 4, s));
+    GB_CUDA(cudaMemsetAsync(r->tile_cnt.p, 0, (size_t)b.ntiles * 4, s));
+    launch(GBLOD_K_RENDER_OTHER, k_bzero, dim3(G), dim3(256), 0, s, (const ViewDev *)dv, n, b.npix);
+    // R1 over (view, node) pairs
+    uint32_t *nsel = r->lvl_cnt.p + b.max_levels + 1;
+    unsigned long long *fin = r->b_frontA.p, *fout = r->b_frontB.p;
+    launch(GBLOD_K_SELECT_NODES, k_bselect_init, dim3(1), dim3(256), 0, s, (const ViewDev *)dv, n, fin, r->lvl_cnt.p);
+    for (uint32_t d = 0; d < b.max_levels; ++d) {
+        launch(GBLOD_K_SELECT_NODES, k_bselect_level, dim3((unsigned)persistent_blocks(2)), dim3(RT), 0, s,
+               (const ViewDev *)dv, (const unsigned long long *)fin, (const uint32_t *)(r->lvl_cnt.p + d), fout,
+               r->lvl_cnt.p + d + 1, r->b_sel.p, nsel);
+        std::swap(fin, fout);
+    }
+    const uint32_t cap = (uint32_t)(b.nodes + 1);
+    launch(GBLOD_K_SELECT_NODES, k_bsel_counts, dim3(G), dim3(256), 0, s, (const ViewDev *)dv,
+           (const unsigned long long *)r->b_sel.p, (const uint32_t *)nsel, cap, r->b_counts.p);
+    scan_exclusive_u64(A, r->scan, reinterpret_cast<const uint64_t *>(r->b_counts.p),
+                       reinterpret_cast<uint64_t *>(r->b_pfx.p), cap, reinterpret_cast<uint64_t *>(&r->stats->points),
+                       s);
+    launch(GBLOD_K_SELECT_NODES, k_bsel_base, dim3(G), dim3(256), 0, s, (const ViewDev *)dv,
+           (const unsigned long long *)r->b_sel.p, (const uint32_t *)nsel, (const unsigned long long *)r->b_pfx.p,
+           r->b_base.p, r->stats);
+    // R2: count, offsets, scatter
+    const SrcBatch src{dv, r->b_sel.p, r->b_pfx.p, r->b_base.p, nsel, &r->stats->points};
+    launch(GBLOD_K_PROJECT_COUNT, k_bproject<false>, dim3(G), dim3(RT), 0, s, src, r->tile_cnt.p,
+           (uint32_t *)nullptr, (uint4 *)nullptr, 0ull, r->status, r->stats);
+    scan_exclusive_u32(A, r->scan, r->tile_cnt.p, r->tile_off.p, b.ntiles, r->tile_off.p + b.ntiles, s);
+    launch(GBLOD_K_RENDER_OTHER, k_tile_items, dim3((b.ntiles + 255) / 256), dim3(256), 0, s, b.ntiles,
+           (const uint32_t *)r->tile_cnt.p, r->item_cnt.p);
+    scan_exclusive_u32(A, r->scan, r->item_cnt.p, r->item_off.p, b.ntiles, r->item_off.p + b.ntiles, s);
+    GB_CUDA(cudaMemcpyAsync(r->tile_cur.p, r->tile_off.p, (size_t)b.ntiles * 4, cudaMemcpyDeviceToDevice, s));
+    launch(GBLOD_K_PROJECT_SCATTER, k_bproject<true>, dim3(G), dim3(RT), 0, s, src, (uint32_t *)nullptr,
+           r->tile_cur.p, r->records.p, (unsigned long long)r->b_rec_cap, r->status, r->stats);
+    launch(GBLOD_K_RENDER_OTHER, k_bfill_items, dim3((b.ntiles + 255) / 256), dim3(256), 0, s, b.ntiles,
+           (const ViewDev *)dv, n, (const uint32_t *)r->tile_cnt.p, (const uint32_t *)r->tile_off.p,
+           (const uint32_t *)r->item_off.p, r->items.p, (uint32_t)items_cap, (unsigned long long)r->b_rec_cap,
+           (const FrameStatsDev *)r->stats, r->status);
+    // R3: persistent over the items of all views
+    launch(GBLOD_K_SPLAT, k_bsplat, dim3(G), dim3(RT), 0, s, (const uint4 *)r->records.p, (const uint4 *)r->items.p,
+           (const uint32_t *)(r->item_off.p + b.ntiles), (uint32_t)items_cap, (const ViewDev *)dv, r->stats);
+    // R4
+    if (rp.tone_auto) {
+        GB_CUDA(cudaMemsetAsync(r->maxv.p, 0, (size_t)n * 8, s));
+        launch(GBLOD_K_TONEMAP, k_bmax, dim3(G), dim3(256), 0, s, (const ViewDev *)dv, n, b.npix, r->maxv.p);
+    }
+    launch(GBLOD_K_TONEMAP, k_btonemap, dim3(G), dim3(256), 0, s, (const ViewDev *)dv, n, b.npix,
+           (const unsigned long long *)r->maxv.p, rp.tone_auto ? 1 : 0);
+}
+
+namespace {
 } // namespace
 
 void renderer_init(gblod_renderer *r, cudaStream_t s)
@@ -853,10 +1356,12 @@ void renderer_release(gblod_renderer *r)
     r->item_cnt.release(A, s); r->item_off.release(A, s);
     r->records.release(A, s); r->items.release(A, s); r->accum.release(A, s); r->maxv.release(A, s);
     r->pass_stats.release(A, s);
+    r->b_views.release(A, s); r->b_frontA.release(A, s); r->b_frontB.release(A, s); r->b_sel.release(A, s);
+    r->b_counts.release(A, s); r->b_pfx.release(A, s); r->b_base.release(A, s);
     r->scan.buf.release(A, s);
 }
 
-static void check_image(const gblod_camera &c)
+void check_image(const gblod_camera &c)
 {
     if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384)
         fail(GBLOD_ERR_INVALID_ARG, "camera width/height must be in 1..16384");

@@ -26,6 +26,11 @@ struct gblod_renderer {
     gb::DBuf<uint4> records, items;
     gb::DBuf<unsigned long long> accum, maxv;
     gb::DBuf<gb::FrameStatsDev> pass_stats; // counters of one range when a frame is split
+    // batched views
+    gb::DBuf<unsigned char> b_views; // per-view device constants (projection, frustum, pointers)
+    gb::DBuf<unsigned long long> b_frontA, b_frontB, b_sel, b_counts, b_pfx;
+    gb::DBuf<long long> b_base;
+    uint64_t b_rec_cap = 0;
     cudaStream_t last_stream = nullptr;
     bool last_was_lod = false;
 };
@@ -41,6 +46,9 @@ void render_brute(gblod_renderer *r, const float *xyz, const float *mass, const 
 gblod_status render_brute_noalloc(const float *xyz, const float *mass, const float *h, uint64_t n,
                                   const gblod_camera &cam, const gblod_render_params &rp, uint8_t *image,
                                   uint64_t *accum, cudaStream_t s);
+void reserve_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod_render_params &rp,
+                   uint64_t record_capacity, cudaStream_t s);
+void render_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod_render_params &rp, cudaStream_t s);
 void project_points(const float4 *pts4, const float *h, uint64_t n, const gblod_camera &cam,
                     const gblod_render_params &rp, int64_t *out, cudaStream_t s);
 void morton_keys(const float *xyz, uint64_t n, const double lo[3], double side, uint64_t *keys, cudaStream_t s);

@@ -189,6 +189,7 @@ const char *gblod_status_string(gblod_status s)
     case GBLOD_ERR_CUDA: return "CUDA error";
     case GBLOD_ERR_DEVICE_TIMEOUT: return "device wait timed out";
     case GBLOD_ERR_NOT_IMPLEMENTED: return "not implemented";
+    case GBLOD_ERR_CAPACITY: return "reserved scratch too small for the batch";
     }
     return "unknown status";
 }

@@ -16,7 +16,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgblod.so")
 
-OK, ERR_INVALID_ARG, ERR_RANGE, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_NOT_IMPLEMENTED = range(7)
+OK, ERR_INVALID_ARG, ERR_RANGE, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_NOT_IMPLEMENTED, ERR_CAPACITY = range(8)
 NODE_LEAF, NODE_INTERNAL, NODE_LOSSY, NODE_REPS = 1, 2, 4, 8
 KERNEL_GAUSSIAN, KERNEL_CUBIC = 0, 1
 (K_ANY, K_MORTON, K_SORT_UPSWEEP, K_SORT_SCATTER, K_SCAN, K_BUILD_OTHER, K_SEL_HIST, K_SEL_MARK, K_SEL_WRITE,
@@ -48,6 +48,10 @@ class RenderParams(C.Structure):
                 ("tone_lo", C.c_double), ("tone_hi", C.c_double), ("kernel", C.c_int32),
                 ("tone_auto", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
                 ("record_budget", C.c_uint64)]
+
+
+class View(C.Structure):
+    _fields_ = [("octree", C.c_void_p), ("camera", Camera), ("d_image", C.c_void_p), ("d_accum", C.c_void_p)]
 
 
 class OctreeInfo(C.Structure):
@@ -90,6 +94,10 @@ _L.gblod_renderer_status.argtypes = [_vp, _vp, C.c_int]
 _L.gblod_renderer_stats.argtypes = [_vp, _vp, C.POINTER(FrameStats)]
 _L.gblod_renderer_last_selection.argtypes = [_vp, _vp, _vp, _u64, C.POINTER(_u64)]
 _L.gblod_morton_keys.argtypes = [_vp, _u64, C.POINTER(_d), _d, _vp, _vp]
+_L.gblod_renderer_reserve_batch.argtypes = [_vp, C.POINTER(View), _i32, C.POINTER(RenderParams), _u64, _vp]
+_L.gblod_render_batch.argtypes = [_vp, C.POINTER(View), _i32, C.POINTER(RenderParams), _vp]
+_L.gblod_autotune_tiles.argtypes = [_vp, C.POINTER(View), _i32, C.POINTER(RenderParams), _u64, _vp,
+                                    C.POINTER(_d)]
 _L.gblod_project.argtypes = [_vp, _vp, _u64, C.POINTER(Camera), C.POINTER(RenderParams), _vp, _vp]
 _L.gblod_launch_count.restype = _u64
 _L.gblod_probe_enable.argtypes = [_i32]
@@ -100,7 +108,7 @@ _L.gblod_last_error.restype = C.c_char_p
 for _f in ("gblod_build_lod", "gblod_octree_get_info", "gblod_octree_export", "gblod_renderer_create",
            "gblod_render", "gblod_render_bruteforce", "gblod_renderer_status", "gblod_renderer_stats",
            "gblod_renderer_last_selection", "gblod_morton_keys", "gblod_project", "gblod_probe_enable",
-           "gblod_probe_read"):
+           "gblod_probe_read", "gblod_renderer_reserve_batch", "gblod_render_batch", "gblod_autotune_tiles"):
     getattr(_L, _f).restype = C.c_int
 
 
@@ -135,7 +143,7 @@ def make_camera(cam: dict) -> Camera:
 
 
 def make_params(lambda_px=None, sigma_min_px=0.5, sigma_max_px=128.0, kernel=KERNEL_GAUSSIAN, tone_auto=True,
-                tone_lo=0.0, tone_hi=0.0, tile_w=16, tile_h=16, record_budget=0) -> RenderParams:
+                tone_lo=0.0, tone_hi=0.0, tile_w=0, tile_h=0, record_budget=0) -> RenderParams:
     p = RenderParams()
     p.lambda_px = -1.0 if lambda_px is None else float(lambda_px)
     p.sigma_min_px, p.sigma_max_px = float(sigma_min_px), float(sigma_max_px)
@@ -245,6 +253,37 @@ class Renderer:
                                             _ptr(acc), _stream(stream))
             _check(st, "gblod_render_bruteforce")
         return img, acc
+
+    # ---- batched views: each view is (octree, camera dict, uint8 image tensor or None, int64 accum tensor)
+    @staticmethod
+    def _views(views):
+        arr = (View * len(views))()
+        for i, (octree, cam, img, acc) in enumerate(views):
+            arr[i].octree = octree.handle
+            arr[i].camera = make_camera(cam)
+            arr[i].d_image = _ptr(img) if img is not None else None
+            arr[i].d_accum = _ptr(acc)
+        return arr
+
+    def reserve_batch(self, views, params: RenderParams | None = None, record_capacity: int = 0, stream=None):
+        params = params if params is not None else make_params()
+        arr = self._views(views)
+        _check(_L.gblod_renderer_reserve_batch(self._h, arr, len(views), C.byref(params), int(record_capacity),
+                                               _stream(stream)), "gblod_renderer_reserve_batch")
+
+    def render_batch(self, views, params: RenderParams | None = None, stream=None):
+        params = params if params is not None else make_params()
+        arr = self._views(views)
+        _check(_L.gblod_render_batch(self._h, arr, len(views), C.byref(params), _stream(stream)),
+               "gblod_render_batch")
+
+    def autotune(self, views, params: RenderParams | None = None, record_capacity: int = 0, stream=None):
+        params = params if params is not None else make_params()
+        arr = self._views(views)
+        best = _d()
+        _check(_L.gblod_autotune_tiles(self._h, arr, len(views), C.byref(params), int(record_capacity),
+                                       _stream(stream), C.byref(best)), "gblod_autotune_tiles")
+        return params, float(best.value)
 
     def status(self, reset: bool = True, stream=None) -> int:
         return int(_L.gblod_renderer_status(self._h, _stream(stream), int(reset)))
