@@ -240,7 +240,8 @@ gblod_status gblod_render_batch(gblod_renderer *r, const gblod_view *views, int3
 
 /* Autotuner: renders the batch with each candidate screen tile (16x16, 32x16, 16x32, 32x32, 64x16)
  * and keeps the fastest in params_inout->tile_w/tile_h (the image is the same for every tile);
- * *best_ms gets its time.  Reserves as needed and waits for `stream`. */
+ * *best_ms gets its time.  Candidates whose records overflow `record_capacity` are not eligible
+ * (GBLOD_ERR_CAPACITY if none fits).  Reserves as needed and waits for `stream`. */
 gblod_status gblod_autotune_tiles(gblod_renderer *r, const gblod_view *views, int32_t n_views,
                                   gblod_render_params *params_inout, uint64_t record_capacity, void *stream,
                                   double *best_ms);

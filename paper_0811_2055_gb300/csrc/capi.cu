@@ -239,6 +239,14 @@ gblod_status gblod_autotune_tiles(gblod_renderer *r, const gblod_view *views, in
             GB_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
             GB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            // a candidate whose records overflow the capacity skipped work: not eligible
+            unsigned bits = 0;
+            GB_CUDA(cudaMemcpy(&bits, r->status, 4, cudaMemcpyDeviceToHost));
+            if (bits & 4u) {
+                const unsigned keep = bits & ~4u;
+                GB_CUDA(cudaMemcpy(r->status, &keep, 4, cudaMemcpyHostToDevice));
+                continue;
+            }
             if (best < 0.0 || ms / 3.0 < best) {
                 best = ms / 3.0;
                 bw = c[0];
@@ -247,6 +255,7 @@ gblod_status gblod_autotune_tiles(gblod_renderer *r, const gblod_view *views, in
         }
         (void)cudaEventDestroy(e0);
         (void)cudaEventDestroy(e1);
+        if (best < 0.0) fail(GBLOD_ERR_CAPACITY, "every tile candidate overflowed the record capacity");
         params_inout->tile_w = bw;
         params_inout->tile_h = bh;
         p.tile_w = bw;
