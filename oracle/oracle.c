@@ -38,6 +38,10 @@
  *   orc_select          lambda = 0 gives every visible leaf, lambda = inf gives the root,
  *                       a camera inside a node refines it, depth falls with distance
  *   orc_tonemap         closed forms on synthetic accumulators
+ *   orc_block_quantize  hand-worked codes, the half-step error bound, lossless decode once the
+ *                       step is below half an ulp, decode-encode round trips, bounds that
+ *                       cover every decoded point, and full depth == brute force of the
+ *                       decoded points
  *
  * parity unpinned: which particular n points a node keeps.  The paper fixes only a
  * "density-weighted random subselection"; the generator (Philox4x32-10 keyed on seed,
@@ -981,6 +985,158 @@ int orc_render_lod(const orc_tree *T, const double lo[3], double side, const orc
     if (n_drawn) *n_drawn = dr;
     if (n_points) *n_points = np;
     return st;
+}
+
+/* ------------------------------------------------------------------ 16-bit block codes */
+/* Storage paragraph: every point's position is kept as 2 bytes per coordinate spanning the
+ * block (node) that holds it, and the other properties are coded the same way.  Readings:
+ *   position  per node: qlo[a] = fp32(corner of the node's cell), qstep = fp32(edge 2^-16);
+ *             code = floor(((double)x - qlo) / qstep) clamped to [0, 65535] (NaN -> 0);
+ *             decode x' = qlo + (code + 1/2) qstep, fp32, one rounding per operation.  A point
+ *             inside its cell comes back within edge 2^-17 (plus the final fp32 rounding);
+ *             once qstep is below half an fp32 ulp of x the decode returns x itself.
+ *   w and h   per node: lo = the smallest finite value, step = fp32((largest - lo) / 65535)
+ *             in double; code = rne(((double)v - lo) / step) clamped to [0, 65535] (0 when
+ *             step is 0 or v is not finite); decode v' = lo + code step, fp32.
+ *   culling   the quantised tree's node bounds and h_cull are recomputed from the decoded
+ *             points of each subtree, so culling stays conservative for what is drawn. */
+static uint16_t orc_code_floor(float x, float lo, float step)
+{
+    double d = ((double)x - (double)lo) / (double)step;
+    if (!(d >= 0.0)) return 0;
+    if (d >= 65535.0) return 65535;
+    return (uint16_t)floor(d);
+}
+
+static uint16_t orc_code_rne(float v, float lo, float step)
+{
+    if (!(step > 0.0f) || !isfinite(v)) return 0;
+    double d = rint(((double)v - (double)lo) / (double)step);
+    if (!(d >= 0.0)) return 0;
+    if (d >= 65535.0) return 65535;
+    return (uint16_t)d;
+}
+
+static float orc_decode_pos(uint16_t c, float lo, float step)
+{
+    float t = (float)c + 0.5f;
+    float m = t * step;
+    return lo + m;
+}
+
+static float orc_decode_lin(uint16_t c, float lo, float step)
+{
+    float m = (float)c * step;
+    return lo + m;
+}
+
+static void orc_range(const float *v, uint64_t n, uint64_t stride, float *lo, float *step)
+{
+    float mn = 0.0f, mx = 0.0f;
+    int any = 0;
+    for (uint64_t j = 0; j < n; ++j) {
+        float x = v[j * stride];
+        if (!isfinite(x)) continue;
+        if (!any || x < mn) mn = x;
+        if (!any || x > mx) mx = x;
+        any = 1;
+    }
+    *lo = mn;
+    *step = (float)(((double)mx - (double)mn) / 65535.0);
+}
+
+/* Encodes every stored point of T.  codes: 5 per point (x, y, z, w, h); qa: 8 floats per node
+ * (qlo x, y, z, qstep, w lo, w step, h lo, h step).  *decoded receives a tree with the same
+ * nodes whose points are the decoded values and whose bmin / bmax / h_cull cover the decoded
+ * points of each subtree (pt_src, skey, sidx are not carried over). */
+int orc_block_quantize(const orc_tree *T, const double lo[3], double side, uint16_t *codes, float *qa,
+                       orc_tree **decoded)
+{
+    uint64_t nn = T->n_nodes, np = T->n_pts;
+    orc_tree *D = (orc_tree *)calloc(1, sizeof(orc_tree));
+    D->nodes = (orc_node *)malloc(sizeof(orc_node) * (nn ? nn : 1));
+    D->pts4 = (float *)malloc(sizeof(float) * 4 * (np ? np : 1));
+    D->hs = (float *)malloc(sizeof(float) * (np ? np : 1));
+    D->n_nodes = nn;
+    D->n_pts = np;
+    D->n = T->n;
+    D->depth_max = T->depth_max;
+    D->equal_mass = T->equal_mass;
+    if (nn) memcpy(D->nodes, T->nodes, sizeof(orc_node) * nn);
+    for (uint64_t i = 0; i < nn; ++i) {
+        const orc_node *nd = &T->nodes[i];
+        double blo[3], bhi[3], e;
+        orc_node_box(nd, lo, side, blo, bhi, &e);
+        float *A = qa + 8 * i;
+        for (int a = 0; a < 3; ++a) A[a] = (float)blo[a];
+        A[3] = (float)ldexp(e, -16);
+        uint64_t p0 = nd->point_first, m = nd->point_count;
+        orc_range(T->pts4 + 4 * p0 + 3, m, 4, &A[4], &A[5]);
+        orc_range(T->hs + p0, m, 1, &A[6], &A[7]);
+        for (uint64_t j = p0; j < p0 + m; ++j) {
+            uint16_t *c = codes + 5 * j;
+            for (int a = 0; a < 3; ++a) c[a] = orc_code_floor(T->pts4[4 * j + a], A[a], A[3]);
+            c[3] = orc_code_rne(T->pts4[4 * j + 3], A[4], A[5]);
+            c[4] = orc_code_rne(T->hs[j], A[6], A[7]);
+            for (int a = 0; a < 3; ++a) D->pts4[4 * j + a] = orc_decode_pos(c[a], A[a], A[3]);
+            D->pts4[4 * j + 3] = orc_decode_lin(c[3], A[4], A[5]);
+            D->hs[j] = orc_decode_lin(c[4], A[6], A[7]);
+        }
+    }
+    /* subtree bounds and h_cull of the decoded points, children before parents */
+    for (uint64_t ii = nn; ii-- > 0;) {
+        orc_node *nd = &D->nodes[ii];
+        float mn[3], mx[3], hm = 0.0f;
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = INFINITY;
+            mx[a] = -INFINITY;
+        }
+        for (uint64_t j = nd->point_first; j < nd->point_first + nd->point_count; ++j) {
+            for (int a = 0; a < 3; ++a) {
+                float x = D->pts4[4 * j + a];
+                if (x < mn[a]) mn[a] = x;
+                if (x > mx[a]) mx[a] = x;
+            }
+            if (D->hs[j] > hm) hm = D->hs[j];
+        }
+        if (nd->flags & ORC_INTERNAL)
+            for (uint32_t k = 0; k < nd->child_count; ++k) {
+                const orc_node *ch = &D->nodes[nd->child_first + k];
+                for (int a = 0; a < 3; ++a) {
+                    if (ch->bmin[a] < mn[a]) mn[a] = ch->bmin[a];
+                    if (ch->bmax[a] > mx[a]) mx[a] = ch->bmax[a];
+                }
+                if (ch->h_cull > hm) hm = ch->h_cull;
+            }
+        for (int a = 0; a < 3; ++a) {
+            nd->bmin[a] = mn[a];
+            nd->bmax[a] = mx[a];
+        }
+        nd->h_cull = hm;
+    }
+    *decoded = D;
+    return ORC_OK;
+}
+
+/* single-value helpers for the tests */
+void orc_block_code_pos(const float *x, uint64_t n, float lo, float step, uint16_t *out)
+{
+    for (uint64_t i = 0; i < n; ++i) out[i] = orc_code_floor(x[i], lo, step);
+}
+
+void orc_block_decode_pos(const uint16_t *c, uint64_t n, float lo, float step, float *out)
+{
+    for (uint64_t i = 0; i < n; ++i) out[i] = orc_decode_pos(c[i], lo, step);
+}
+
+void orc_block_code_lin(const float *v, uint64_t n, float lo, float step, uint16_t *out)
+{
+    for (uint64_t i = 0; i < n; ++i) out[i] = orc_code_rne(v[i], lo, step);
+}
+
+void orc_block_decode_lin(const uint16_t *c, uint64_t n, float lo, float step, float *out)
+{
+    for (uint64_t i = 0; i < n; ++i) out[i] = orc_decode_lin(c[i], lo, step);
 }
 
 /* ------------------------------------------------------------------ tone map */

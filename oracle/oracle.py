@@ -112,6 +112,13 @@ def lib():
         L.orc_render_lod.restype = C.c_int
         L.orc_tonemap.argtypes = [u64p, C.c_uint64, P(RParams), np.ctypeslib.ndpointer(np.uint8, flags="C")]
         L.orc_constants.argtypes = [np.ctypeslib.ndpointer(np.float32, flags="C")]
+        u16p = np.ctypeslib.ndpointer(np.uint16, flags="C")
+        L.orc_block_quantize.argtypes = [P(Tree), f64p, C.c_double, u16p, f32p, P(P(Tree))]
+        L.orc_block_quantize.restype = C.c_int
+        for nm in ("orc_block_code_pos", "orc_block_code_lin"):
+            getattr(L, nm).argtypes = [f32p, C.c_uint64, C.c_float, C.c_float, u16p]
+        for nm in ("orc_block_decode_pos", "orc_block_decode_lin"):
+            getattr(L, nm).argtypes = [u16p, C.c_uint64, C.c_float, C.c_float, f32p]
         _lib = L
     return _lib
 
@@ -231,10 +238,10 @@ class OracleTree:
                       if nn else np.zeros(0, NODE_DTYPE))
         self.pts4 = np.ctypeslib.as_array(T.pts4, (max(npt, 1) * 4,))[: npt * 4].reshape(npt, 4).copy()
         self.hs = np.ctypeslib.as_array(T.hs, (max(npt, 1),))[:npt].copy()
-        self.pt_src = np.ctypeslib.as_array(T.pt_src, (max(npt, 1),))[:npt].copy()
+        self.pt_src = np.ctypeslib.as_array(T.pt_src, (max(npt, 1),))[:npt].copy() if T.pt_src else None
         n = self.n
-        self.skey = np.ctypeslib.as_array(T.skey, (max(n, 1),))[:n].copy()
-        self.sidx = np.ctypeslib.as_array(T.sidx, (max(n, 1),))[:n].copy()
+        self.skey = np.ctypeslib.as_array(T.skey, (max(n, 1),))[:n].copy() if T.skey else None
+        self.sidx = np.ctypeslib.as_array(T.sidx, (max(n, 1),))[:n].copy() if T.sidx else None
         self.depth_max = int(T.depth_max)
         self.equal_mass = bool(T.equal_mass)
 
@@ -333,6 +340,49 @@ def pixel_value(pts4, hs, cam: dict, rp: RParams, px: int, py: int) -> int:
     pts4 = np.ascontiguousarray(pts4, np.float32).reshape(-1, 4)
     return int(lib().orc_pixel_value(pts4, np.ascontiguousarray(hs, np.float32), pts4.shape[0],
                                      C.byref(camera(cam)), C.byref(rp), px, py))
+
+
+def block_quantize(tree: OracleTree):
+    """16-bit block codes of every stored point (storage paragraph): returns codes (n_pts x 5 uint16:
+    x, y, z, w, h), per-node constants (n_nodes x 8 float32: qlo x y z, qstep, w lo, w step, h lo,
+    h step) and the decoded tree (same nodes, decoded points, bounds and h_cull of the decoded
+    subtrees)."""
+    npt, nn = len(tree.pts4), len(tree.nodes)
+    codes = np.zeros((max(npt, 1), 5), np.uint16)
+    qa = np.zeros((max(nn, 1), 8), np.float32)
+    out = C.POINTER(Tree)()
+    st = lib().orc_block_quantize(tree._ptr, tree.lo, tree.side, codes, qa, C.byref(out))
+    if st != 0:
+        raise RuntimeError(f"orc_block_quantize failed: {st}")
+    return codes[:npt], qa[:nn], OracleTree(out, tree.lo, tree.side, tree.n_max, tree.seed)
+
+
+def block_code_pos(x, lo: float, step: float) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float32).reshape(-1)
+    out = np.zeros(max(x.size, 1), np.uint16)
+    lib().orc_block_code_pos(x, x.size, lo, step, out)
+    return out[: x.size]
+
+
+def block_decode_pos(c, lo: float, step: float) -> np.ndarray:
+    c = np.ascontiguousarray(c, np.uint16).reshape(-1)
+    out = np.zeros(max(c.size, 1), np.float32)
+    lib().orc_block_decode_pos(c, c.size, lo, step, out)
+    return out[: c.size]
+
+
+def block_code_lin(v, lo: float, step: float) -> np.ndarray:
+    v = np.ascontiguousarray(v, np.float32).reshape(-1)
+    out = np.zeros(max(v.size, 1), np.uint16)
+    lib().orc_block_code_lin(v, v.size, lo, step, out)
+    return out[: v.size]
+
+
+def block_decode_lin(c, lo: float, step: float) -> np.ndarray:
+    c = np.ascontiguousarray(c, np.uint16).reshape(-1)
+    out = np.zeros(max(c.size, 1), np.float32)
+    lib().orc_block_decode_lin(c, c.size, lo, step, out)
+    return out[: c.size]
 
 
 def tonemap(acc, rp: RParams) -> np.ndarray:
