@@ -38,7 +38,11 @@ def args_():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mid", "paper", "tiny"], default="mid")
+    ap.add_argument("--no-block16", action="store_true", help="skip the 16-bit block-code fly-through")
+    ap.add_argument("--workload", choices=["mid", "paper", "tiny", "diff", "serve"], default="mid")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of offered load")
+    ap.add_argument("--sessions", type=int, default=64)
+    ap.add_argument("--session-budget-gb", type=float, default=4.0)
     ap.add_argument("--frames", type=int, default=0, help="frames per step (0 = the workload's path)")
     ap.add_argument("--particles", type=int, default=0, help="particles (0 = the workload's size)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -255,6 +259,52 @@ def run_ours(a):
                                                           probe=gblod.K_SPLAT)
     ck = clocks.stop()
 
+    # 16-bit block codes (storage paragraph): the same fly-through drawn from 10-byte points
+    block16 = None
+    if not a.no_block16:
+        tree = gblod.build_lod(xyz, mass, h, n_max=n_max, seed=1)
+        bytes_f = int(tree.info().device_bytes)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record()
+        tree.quantize(drop_float=True)
+        q1.record()
+        torch.cuda.synchronize()
+        q_ms = q0.elapsed_time(q1)
+        bytes_q = int(tree.info().device_bytes)
+        par_q = gblod.make_params(lambda_px=lam, point_format=gblod.POINTS_BLOCK16)
+        vq = []
+        for cam in cams[:: max(1, nf // 8)]:
+            li, _ = r.render(tree, cam, par_q)
+            bi, _ = r.render_bruteforce(xyz, mass, h, cam, par)
+            d = (li.int() - bi.int()).abs().double()
+            mse = float((d * d).mean())
+            vq.append((float(d.max()), 10 * math.log10(255.0 ** 2 / mse) if mse > 0 else float("inf")))
+        for cam in cams[: min(nf, 16)]:
+            r.render(tree, cam, par_q, image=img, accum=acc)
+        torch.cuda.synchronize()
+        qf_ms = []
+        qt_ms = 0.0
+        for _ in range(a.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * nf)]
+            for k, cam in enumerate(cams):
+                ev[2 * k].record()
+                r.render(tree, cam, par_q, image=img, accum=acc)
+                ev[2 * k + 1].record()
+            torch.cuda.synchronize()
+            ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(nf)]
+            qf_ms += ms
+            qt_ms += ev[0].elapsed_time(ev[-1])
+        assert r.status() == gblod.OK
+        tree.free()
+        block16 = {"bytes_per_point": 10, "bytes_per_point_fp32": 20,
+                   "octree_device_bytes_fp32": bytes_f, "octree_device_bytes_block16_only": bytes_q,
+                   "quantize_ms": q_ms, "frames_per_s_excl_build": a.steps * nf / (qt_ms / 1e3),
+                   "p50_ms": float(np.percentile(qf_ms, 50)), "p99_ms": float(np.percentile(qf_ms, 99)),
+                   "vs_all_points_max_abs_u8": max(v[0] for v in vq),
+                   "vs_all_points_psnr_db_mean": float(np.mean([v[1] for v in vq]))}
+
     brute = None
     if not a.no_brute:
         b_counts = {"splats": 0, "pixel_updates": 0}
@@ -391,6 +441,7 @@ def run_ours(a):
         "build": {"ms": float(np.median(build_ms)), "particles_per_s": p.n / (np.median(build_ms) / 1e3)},
         "visual_equivalence": visual,
         "all_points": brute,
+        "block16": block16,
         "batched": batched,
         "clocks": ck,
         "e2e": e2e,
@@ -460,12 +511,138 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def fibonacci_views(n: int, radius: float = 1.5, size: int = 256):
+    from paper_0811_2055_gb300 import synth
+    out = []
+    g = math.pi * (3.0 - math.sqrt(5.0))
+    for k in range(n):
+        y = 1.0 - 2.0 * (k + 0.5) / n
+        rr = math.sqrt(max(0.0, 1.0 - y * y))
+        e = (0.5 + radius * rr * math.cos(g * k), 0.5 + radius * y, 0.5 + radius * rr * math.sin(g * k))
+        out.append(synth.look_at(e, (0.5, 0.5, 0.5), width=size, height=size))
+    return out
+
+
+def run_diff(a):
+    """Differentiation workload: fit a 1M-point representative set (xyz, weight, log h) so that its
+    float-splat images match those of a 2^24-particle parent from 256 views at 256x256 (L2 loss,
+    Adam, gradients from the adjoint splat kernel).  One step = forward + adjoint over all views."""
+    import torch
+
+    from paper_0811_2055_gb300 import gblod, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n_parent = a.particles or (1 << 24)
+    parent = synth.mid(n_parent, seed=synth.SEED_BASE + 3)
+    n_rep = max(1, n_parent // 16)
+    cams = fibonacci_views(256)
+    r = gblod.Renderer()
+    par = gblod.make_params()
+    pxyz, pw = (torch.from_numpy(x).to(dev) for x in (parent.xyz, parent.mass))
+    pl = torch.from_numpy(np.log(np.maximum(parent.h, 1e-6)).astype(np.float32)).to(dev)
+    t0 = time.perf_counter()
+    target = gblod.diff_render(r, pxyz, pw, pl, cams, par)
+    torch.cuda.synchronize()
+    t_target = time.perf_counter() - t0
+    rng = np.random.Generator(np.random.Philox(key=synth.SEED_BASE + 33))
+    pick = rng.choice(parent.n, n_rep, replace=False)
+    scale = parent.n / n_rep
+    x = torch.tensor(parent.xyz[pick], device=dev, requires_grad=True)
+    wv = torch.full((n_rep,), float(parent.mass.sum()) / n_rep, device=dev, requires_grad=True)
+    lh = torch.tensor(np.log(np.maximum(parent.h[pick], 1e-6) * scale ** (1 / 3)).astype(np.float32), device=dev,
+                      requires_grad=True)
+    opt = torch.optim.Adam([{"params": [x], "lr": 1e-4}, {"params": [wv], "lr": 0.05}, {"params": [lh], "lr": 5e-3}])
+    losses = []
+
+    def step():
+        opt.zero_grad()
+        img = gblod.SplatImages.apply(x, wv, lh, cams, r, par)
+        loss = ((img - target) ** 2).sum()
+        loss.backward()
+        opt.step()
+        return loss.detach()
+
+    for _ in range(a.warmup):
+        losses.append(float(step()))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        losses.append(float(step()))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    line = {"metric": "views/s, forward + adjoint float splat (fit of LOD representatives)",
+            "value": len(cams) / (ms / 1e3), "unit": "views/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"diff: {n_rep} representatives fitted to a {parent.n}-particle mid-recipe parent, "
+                                   "256 views on a Fibonacci sphere of radius 1.5, 256x256, L2 image loss, Adam",
+                       "views": len(cams), "resolution": "256x256"},
+            "target_render_s": t_target, "loss_first": losses[0], "loss_last": losses[-1],
+            "loss_curve": losses}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(a):
+    """Serving workload: 16 device-resident timesteps (halo drift), 64 viewer sessions at mixed
+    resolutions (720p/1080p/4K) with Poisson requests at 30 Hz each, admission by an HBM budget,
+    continuous batching over two streams; a newer request of a session supersedes its queued one."""
+    import torch
+
+    from paper_0811_2055_gb300 import gblod, serve, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = a.particles or 75_000_000
+    t0 = time.perf_counter()
+    base = synth.timesteps_recipe(n)
+    t_gen = time.perf_counter() - t0
+    x0, vel = torch.from_numpy(base.xyz).to(dev), torch.from_numpy(base.vel).to(dev)
+    mass, h = torch.from_numpy(base.mass).to(dev), torch.from_numpy(base.h).to(dev)
+    del base
+    trees = []
+    t0 = time.perf_counter()
+    for t in range(16):
+        xt = torch.remainder(x0 + t * vel, 1.0).contiguous()
+        trees.append(gblod.build_lod(xt, mass, h, n_max=16000, seed=1))
+        del xt
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    del x0, vel
+    res_choices = [(1280, 720), (1920, 1080), (3840, 2160)]
+    res, reqs = serve.poisson_requests(a.sessions, 30.0, a.duration, len(trees), res_choices, seed=0)
+    loop = serve.ServingLoop(trees, hbm_budget_bytes=int(a.session_budget_gb * (1 << 30)), max_views=16,
+                             record_capacity=1 << 30, supersede=True)
+    admitted = [loop.admit(s, w, hh) for s, (w, hh) in enumerate(res)]
+    loop.reserve([(trees[0], synth.look_at((0.5, 0.5, -1), (0.5, 0.5, 0.5), width=3840, height=2160))] * 16)
+    done = loop.run(reqs, a.duration)
+    st = serve.latency_stats(done, a.duration)
+    offered = sum(1 for q in reqs if admitted[q.session])
+    line = {"metric": "serving: frames/s and p50/p99 frame latency (arrival -> 8-bit image on the host)",
+            "value": st.get("frames_per_s", 0.0), "unit": "frames/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/u64", "data": "synthetic",
+            "config": {"workload": f"serve: 16 timesteps x {n} particles (32,768 drifting NFW halos + 10% uniform), "
+                                   f"{a.sessions} sessions at 720p/1080p/4K, Poisson 30 Hz each, {a.duration} s",
+                       "session_budget_gb": a.session_budget_gb, "max_views_per_batch": 16, "streams": 2},
+            "p50_ms": st.get("p50_ms"), "p99_ms": st.get("p99_ms"), "completed": st.get("completed", 0),
+            "sessions_admitted": int(sum(admitted)), "sessions_rejected": int(len(admitted) - sum(admitted)),
+            "requests_offered_admitted": offered, "superseded": loop.stats["superseded"],
+            "batches": loop.stats["batches"], "overflow_batches": loop.stats["overflow_batches"],
+            "generate_s": t_gen, "build_16_timesteps_s": t_build}
+    loop.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = args_()
     if a.warmup < 3:
         a.warmup = 3
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "diff":
+        run_diff(a)
+    elif a.workload == "serve":
+        run_serve(a)
     else:
         run_ours(a)
 

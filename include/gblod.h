@@ -106,7 +106,7 @@ typedef struct {
     int32_t depth_max;
     int32_t equal_mass;   /* 1 if every particle had the same mass (raw draws are the keys) */
     uint32_t n_max;
-    uint32_t reserved;
+    uint32_t formats;     /* bit 0: fp32 points held; bit 1: 16-bit block codes held */
 } gblod_octree_info;
 
 /* Builds the octree on the device (octree paragraph; A1 Morton keys, A2 radix sort, A3 node
@@ -137,6 +137,39 @@ gblod_status gblod_octree_get_info(const gblod_octree *octree, gblod_octree_info
 gblod_status gblod_octree_export(const gblod_octree *octree, gblod_node *h_nodes, float *h_pts4, float *h_hs,
                                  uint32_t *h_pt_src, uint64_t *h_skey, uint32_t *h_sidx);
 
+/* ----------------------------------------------------------------- 16-bit block codes */
+/* Storage paragraph: positions are kept in 2 bytes per coordinate spanning the block (node)
+ * that holds the point, and the other properties are coded the same way, which halves the
+ * bytes read per drawn point (10 instead of 20).  Codes, per node i and stored point j:
+ *   qa[i] = (qlo_x, qlo_y, qlo_z, qstep, w_lo, w_step, h_lo, h_step)  8 floats
+ *     qlo = fp32(corner of the node's cell), qstep = fp32(edge 2^-16);
+ *     w_lo / h_lo = smallest finite value among the node's points (+0 for a zero),
+ *     *_step = fp32((largest - smallest) / 65535) computed in double (0 if none finite).
+ *   position code c = floor(((double)x - qlo) / qstep) clamped to 0..65535, NaN -> 0;
+ *     decoded x' = qlo + (c + 1/2) qstep   (fp32, each operation rounded to nearest, no FMA);
+ *   w and h codes c = rne(((double)v - lo) / step) clamped to 0..65535 (0 when the step is 0
+ *     or v is not finite); decoded v' = lo + c step  (fp32, no FMA).
+ * A point inside its cell decodes within edge 2^-17 of itself (plus the final fp32 rounding);
+ * a point outside the root cube (clamped into a boundary cell by the build) decodes inside the
+ * cell.  The quantised node table is the octree's own with bmin / bmax / h_cull replaced by the
+ * bounds and the largest decoded h of the decoded points of each subtree, so culling stays
+ * conservative for what is drawn. */
+#define GBLOD_POINTS_FLOAT 0   /* fp32 (x, y, z, w) + h: 20 bytes per point */
+#define GBLOD_POINTS_BLOCK16 1 /* 16-bit block codes: 10 bytes per point (gblod_octree_quantize) */
+
+#define GBLOD_QUANTIZE_DROP_FLOAT 1u /* free the fp32 points once coded (GBLOD_POINTS_FLOAT then fails) */
+
+/* Codes every stored point of the octree on the device (enqueued on `stream`, which it then
+ * synchronises) and keeps the codes with the octree.  Calling it again is a no-op apart from
+ * `flags`.  GBLOD_ERR_INVALID_ARG if the fp32 points were already dropped and no codes exist. */
+gblod_status gblod_octree_quantize(gblod_octree *octree, uint32_t flags, void *stream);
+
+/* Copies the block codes to host buffers (each may be NULL): h_codes n_points x 5 uint16
+ * (x, y, z, w, h); h_qa n_nodes x 8 float (see above); h_qnodes n_nodes gblod_node, the
+ * quantised node table.  Synchronous.  GBLOD_ERR_INVALID_ARG if the octree holds no codes. */
+gblod_status gblod_octree_export_block16(const gblod_octree *octree, uint16_t *h_codes, float *h_qa,
+                                         gblod_node *h_qnodes);
+
 /* ----------------------------------------------------------------- rendering */
 /* Pinhole camera (depth paragraph; GPU paragraph).  right/up/fwd are orthonormal rows;
  * image coordinates: u = cx + f_px * x_c / z_c, v = cy - f_px * y_c / z_c (y points down);
@@ -164,6 +197,8 @@ typedef struct {
     uint64_t record_budget; /* most (tile, splat) records held at once (16 bytes each); 0 = 2^28,
                              capped at 2^31.  A frame needing more is binned and splatted in
                              several passes over ranges of its points, with the same image */
+    int32_t point_format; /* GBLOD_POINTS_*: which stored form of the octree's points is drawn */
+    int32_t reserved;     /* 0 */
 } gblod_render_params;
 
 /* Render workspace: scratch buffers (grown on demand through the allocator), the sticky
@@ -177,11 +212,15 @@ void gblod_renderer_destroy(gblod_renderer *r);
 /* LOD frame (R1 node selection, R2 projection and binning, R3 tiled splat, R4 tone map).
  *   d_image  height x width uint8 (row-major) or NULL; d_accum height x width uint64
  *   fixed-point intensities (2^-32 units) or NULL (then an internal buffer is used).
- *   Enqueued on `stream`; the call waits once on `stream` mid-frame to size the splat lists. */
+ *   Enqueued on `stream`; the call waits once on `stream` mid-frame to size the splat lists.
+ *   params->point_format GBLOD_POINTS_BLOCK16 selects with the quantised node table and draws
+ *   the decoded codes (the image then equals the oracle's render of the decoded points);
+ *   GBLOD_ERR_INVALID_ARG if the octree does not hold the chosen form. */
 gblod_status gblod_render(gblod_renderer *r, const gblod_octree *octree, const gblod_camera *camera,
                           const gblod_render_params *params, uint8_t *d_image, uint64_t *d_accum, void *stream);
 
-/* Brute-force frame: R2-R4 over every particle (d_xyz n x 3, d_mass n, d_h n), no tree. */
+/* Brute-force frame: R2-R4 over every particle (d_xyz n x 3, d_mass n, d_h n), no tree
+ * (params->point_format is ignored: the fp32 particles are drawn). */
 gblod_status gblod_render_bruteforce(gblod_renderer *r, const float *d_xyz, const float *d_mass, const float *d_h,
                                      uint64_t n, const gblod_camera *camera, const gblod_render_params *params,
                                      uint8_t *d_image, uint64_t *d_accum, void *stream);
@@ -223,6 +262,7 @@ typedef struct {
 
 /* Sizes the renderer's batch scratch for batches no larger than `views` (node counts, tiles,
  * pixels) with room for `record_capacity` (tile, splat) records (0 = 2^28, at most 2^32 - 1).
+ * A batch holds 1..65535 views.
  * Allocates; waits for `stream`. */
 gblod_status gblod_renderer_reserve_batch(gblod_renderer *r, const gblod_view *views, int32_t n_views,
                                           const gblod_render_params *params, uint64_t record_capacity,
@@ -241,10 +281,36 @@ gblod_status gblod_render_batch(gblod_renderer *r, const gblod_view *views, int3
 /* Autotuner: renders the batch with each candidate screen tile (16x16, 32x16, 16x32, 32x32, 64x16)
  * and keeps the fastest in params_inout->tile_w/tile_h (the image is the same for every tile);
  * *best_ms gets its time.  Candidates whose records overflow `record_capacity` are not eligible
- * (GBLOD_ERR_CAPACITY if none fits).  Reserves as needed and waits for `stream`. */
+ * (GBLOD_ERR_CAPACITY if none fits).  Reserves as needed and waits for `stream`.  The winner is
+ * cached per (device, multiset of view resolutions, kernel, point format, record capacity,
+ * power-of-two class of the batch's drawn splats, measured by one render with the caller's tile);
+ * a later call with the same key renders once and returns the cached tile and time. */
 gblod_status gblod_autotune_tiles(gblod_renderer *r, const gblod_view *views, int32_t n_views,
                                   gblod_render_params *params_inout, uint64_t record_capacity, void *stream,
                                   double *best_ms);
+
+/* Forgets every cached autotuner result (process-wide). */
+void gblod_autotune_cache_clear(void);
+
+/* ----------------------------------------------------------------- differentiation */
+/* Float splat of n points (d_xyz n x 3, weights d_w n, log smoothing lengths d_logh n) into
+ * n_views images of one resolution (d_images n_views x height x width float32, overwritten).
+ * Reading for fitting representatives to the full-data image (abstract: the LOD image should be
+ * indistinguishable from a full rendering): sigma = clamp(f exp(l)/z_c, sigma_min, sigma_max),
+ * kernel (exp(-r^2/2 sigma^2) - e^-4.5) / (2 pi sigma^2 (1 - 5.5 e^-4.5)) for r < 3 sigma,
+ * fp32 accumulation (sum order not fixed: results agree to rounding, not bit for bit).  Waits for
+ * `stream` once per chunk of views to size its scratch. */
+gblod_status gblod_diff_render(gblod_renderer *r, const float *d_xyz, const float *d_w, const float *d_logh,
+                               uint64_t n, const gblod_camera *cams, int32_t n_views,
+                               const gblod_render_params *params, float *d_images, void *stream);
+
+/* Adjoint of gblod_diff_render: given dL/dI (d_grad_images, same layout as d_images), writes
+ * dL/dxyz (n x 3), dL/dw (n) and dL/dlog h (n) (overwritten; zero through a sigma clamp).  Every
+ * per-pixel term is recomputed tile by tile; nothing per pixel is stored between the calls. */
+gblod_status gblod_diff_backward(gblod_renderer *r, const float *d_xyz, const float *d_w, const float *d_logh,
+                                 uint64_t n, const gblod_camera *cams, int32_t n_views,
+                                 const gblod_render_params *params, const float *d_grad_images, float *d_grad_xyz,
+                                 float *d_grad_w, float *d_grad_logh, void *stream);
 
 /* ----------------------------------------------------------------- fixed-scratch variant */
 /* Brute-force frame that allocates no memory.  The paper has no counterpart: this entry point

@@ -1041,7 +1041,7 @@ static void orc_range(const float *v, uint64_t n, uint64_t stride, float *lo, fl
         if (!any || x > mx) mx = x;
         any = 1;
     }
-    *lo = mn;
+    *lo = mn + 0.0f; /* a zero lower bound is stored as +0 whichever zero came first */
     *step = (float)(((double)mx - (double)mn) / 65535.0);
 }
 

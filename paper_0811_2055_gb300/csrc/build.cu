@@ -384,6 +384,10 @@ void free_octree(gblod_octree *o)
     o->A.put(o->pt_src, o->n_points * sizeof(uint32_t), s);
     o->A.put(o->skey, o->n * sizeof(uint64_t), s);
     o->A.put(o->sidx, o->n * sizeof(uint32_t), s);
+    o->A.put(o->q4, o->n_points * sizeof(ushort4), s);
+    o->A.put(o->qw, o->n_points * sizeof(uint16_t), s);
+    o->A.put(o->qa, 2 * o->n_nodes * sizeof(float4), s);
+    o->A.put(o->qnodes, o->n_nodes * sizeof(gblod_node), s);
     delete o;
 }
 

@@ -1,7 +1,12 @@
 // The C ABI declared in include/gblod.h: host-side argument checks, then the device work.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "render.cuh"
 
@@ -55,7 +60,25 @@ gblod_render_params check_params(const gblod_render_params *p)
         fail(GBLOD_ERR_INVALID_ARG, "tile must be 1..64 x 1..64 and cover at most 32 blocks of 8 x 4 pixels");
     if (!q.tone_auto && !(q.tone_hi > q.tone_lo && q.tone_lo > 0.0 && std::isfinite(q.tone_hi)))
         fail(GBLOD_ERR_INVALID_ARG, "fixed tone range needs 0 < tone_lo < tone_hi < inf");
+    if (q.point_format != GBLOD_POINTS_FLOAT && q.point_format != GBLOD_POINTS_BLOCK16)
+        fail(GBLOD_ERR_INVALID_ARG, "unknown point_format");
+    if (q.reserved != 0) fail(GBLOD_ERR_INVALID_ARG, "render params reserved field must be 0");
     return q;
+}
+
+struct TuneEntry {
+    int w, h;
+    double ms;
+};
+std::map<std::string, TuneEntry> &tune_cache()
+{
+    static std::map<std::string, TuneEntry> m;
+    return m;
+}
+std::mutex &tune_mutex()
+{
+    static std::mutex m;
+    return m;
 }
 
 } // namespace
@@ -101,6 +124,7 @@ gblod_status gblod_octree_get_info(const gblod_octree *o, gblod_octree_info *out
     i.depth_max = o->depth_max;
     i.equal_mass = o->equal_mass;
     i.n_max = o->n_max;
+    i.formats = (o->has_float ? 1u : 0u) | (o->has_block16 ? 2u : 0u);
     *out = i;
     return GBLOD_OK;
 }
@@ -113,6 +137,8 @@ gblod_status gblod_octree_export(const gblod_octree *o, gblod_node *h_nodes, flo
         cudaStream_t s = o->stream;
         if (h_nodes && o->n_nodes)
             GB_CUDA(cudaMemcpyAsync(h_nodes, o->nodes, o->n_nodes * sizeof(gblod_node), cudaMemcpyDeviceToHost, s));
+        if ((h_pts4 || h_hs) && !o->has_float)
+            fail(GBLOD_ERR_INVALID_ARG, "octree holds no fp32 points (dropped after quantisation)");
         if (h_pts4 && o->n_points)
             GB_CUDA(cudaMemcpyAsync(h_pts4, o->pts4, o->n_points * sizeof(float4), cudaMemcpyDeviceToHost, s));
         if (h_hs && o->n_points)
@@ -121,6 +147,43 @@ gblod_status gblod_octree_export(const gblod_octree *o, gblod_node *h_nodes, flo
             GB_CUDA(cudaMemcpyAsync(h_pt_src, o->pt_src, o->n_points * 4, cudaMemcpyDeviceToHost, s));
         if (h_skey && o->n) GB_CUDA(cudaMemcpyAsync(h_skey, o->skey, o->n * 8, cudaMemcpyDeviceToHost, s));
         if (h_sidx && o->n) GB_CUDA(cudaMemcpyAsync(h_sidx, o->sidx, o->n * 4, cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+gblod_status gblod_octree_quantize(gblod_octree *o, uint32_t flags, void *stream)
+{
+    return guarded([&] {
+        if (!o) fail(GBLOD_ERR_INVALID_ARG, "octree is NULL");
+        if (flags & ~GBLOD_QUANTIZE_DROP_FLOAT) fail(GBLOD_ERR_INVALID_ARG, "unknown quantize flags");
+        block_quantize(o, flags, (cudaStream_t)stream);
+    });
+}
+
+gblod_status gblod_octree_export_block16(const gblod_octree *o, uint16_t *h_codes, float *h_qa, gblod_node *h_qnodes)
+{
+    return guarded([&] {
+        if (!o) fail(GBLOD_ERR_INVALID_ARG, "octree is NULL");
+        if (!o->has_block16) fail(GBLOD_ERR_INVALID_ARG, "octree holds no 16-bit block codes");
+        cudaStream_t s = o->stream;
+        const size_t np = o->n_points, nn = o->n_nodes;
+        if (h_codes && np) {
+            std::vector<ushort4> q4(np);
+            std::vector<uint16_t> qw(np);
+            GB_CUDA(cudaMemcpyAsync(q4.data(), o->q4, np * sizeof(ushort4), cudaMemcpyDeviceToHost, s));
+            GB_CUDA(cudaMemcpyAsync(qw.data(), o->qw, np * sizeof(uint16_t), cudaMemcpyDeviceToHost, s));
+            GB_CUDA(cudaStreamSynchronize(s));
+            for (size_t j = 0; j < np; ++j) {
+                h_codes[5 * j] = q4[j].x;
+                h_codes[5 * j + 1] = q4[j].y;
+                h_codes[5 * j + 2] = q4[j].z;
+                h_codes[5 * j + 3] = qw[j];
+                h_codes[5 * j + 4] = q4[j].w;
+            }
+        }
+        if (h_qa && nn) GB_CUDA(cudaMemcpyAsync(h_qa, o->qa, nn * 2 * sizeof(float4), cudaMemcpyDeviceToHost, s));
+        if (h_qnodes && nn)
+            GB_CUDA(cudaMemcpyAsync(h_qnodes, o->qnodes, nn * sizeof(gblod_node), cudaMemcpyDeviceToHost, s));
         GB_CUDA(cudaStreamSynchronize(s));
     });
 }
@@ -223,6 +286,41 @@ gblod_status gblod_autotune_tiles(gblod_renderer *r, const gblod_view *views, in
         for (int i = 0; i < n_views; ++i) check_camera(&views[i].camera);
         static const int cand[][2] = {{16, 16}, {32, 16}, {16, 32}, {32, 32}, {64, 16}};
         cudaStream_t s = (cudaStream_t)stream;
+        // cache key: device, the views' resolutions, the batch's splat-count class and the parameters
+        // that change the work; one render with the caller's tile measures the splat count
+        reserve_batch(r, views, n_views, p, record_capacity, s);
+        render_batch(r, views, n_views, p, s);
+        unsigned long long splats = 0;
+        GB_CUDA(cudaMemcpyAsync(&splats, &r->stats->splats, 8, cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        {
+            unsigned bits = 0; // this render only measures; an overflow here is not the caller's
+            GB_CUDA(cudaMemcpy(&bits, r->status, 4, cudaMemcpyDeviceToHost));
+            const unsigned keep = bits & ~4u;
+            if (keep != bits) GB_CUDA(cudaMemcpy(r->status, &keep, 4, cudaMemcpyHostToDevice));
+        }
+        int dev = 0;
+        GB_CUDA(cudaGetDevice(&dev));
+        cudaDeviceProp prop;
+        GB_CUDA(cudaGetDeviceProperties(&prop, dev));
+        std::vector<long long> res;
+        for (int i = 0; i < n_views; ++i) res.push_back((long long)views[i].camera.width << 20 | views[i].camera.height);
+        std::sort(res.begin(), res.end());
+        std::string key = std::to_string(dev) + ":" + prop.name + ":" + std::to_string(p.kernel) + ":" +
+                          std::to_string(p.point_format) + ":" + std::to_string(record_capacity) + ":" +
+                          std::to_string(63 - __builtin_clzll(splats | 1ull));
+        for (long long v : res) key += ":" + std::to_string(v);
+        {
+            std::lock_guard<std::mutex> g(tune_mutex());
+            auto it = tune_cache().find(key);
+            if (it != tune_cache().end()) {
+                params_inout->tile_w = p.tile_w = it->second.w;
+                params_inout->tile_h = p.tile_h = it->second.h;
+                reserve_batch(r, views, n_views, p, record_capacity, s);
+                if (best_ms) *best_ms = it->second.ms;
+                return;
+            }
+        }
         cudaEvent_t e0, e1;
         GB_CUDA(cudaEventCreate(&e0));
         GB_CUDA(cudaEventCreate(&e1));
@@ -262,6 +360,44 @@ gblod_status gblod_autotune_tiles(gblod_renderer *r, const gblod_view *views, in
         p.tile_h = bh;
         reserve_batch(r, views, n_views, p, record_capacity, s);
         if (best_ms) *best_ms = best;
+        std::lock_guard<std::mutex> g(tune_mutex());
+        tune_cache()[key] = TuneEntry{bw, bh, best};
+    });
+}
+
+void gblod_autotune_cache_clear(void)
+{
+    std::lock_guard<std::mutex> g(tune_mutex());
+    tune_cache().clear();
+}
+
+gblod_status gblod_diff_render(gblod_renderer *r, const float *d_xyz, const float *d_w, const float *d_logh,
+                               uint64_t n, const gblod_camera *cams, int32_t n_views,
+                               const gblod_render_params *params, float *d_images, void *stream)
+{
+    return guarded([&] {
+        if (!r || !cams || n_views < 1 || !d_images) fail(GBLOD_ERR_INVALID_ARG, "bad arguments");
+        if (n > 0 && (!d_xyz || !d_w || !d_logh)) fail(GBLOD_ERR_INVALID_ARG, "point arrays must not be NULL");
+        const gblod_render_params p = check_params(params);
+        for (int i = 0; i < n_views; ++i) check_camera(&cams[i]);
+        diff_pass(r, d_xyz, d_w, d_logh, n, cams, n_views, p, d_images, nullptr, nullptr, nullptr, nullptr,
+                  (cudaStream_t)stream);
+    });
+}
+
+gblod_status gblod_diff_backward(gblod_renderer *r, const float *d_xyz, const float *d_w, const float *d_logh,
+                                 uint64_t n, const gblod_camera *cams, int32_t n_views,
+                                 const gblod_render_params *params, const float *d_grad_images, float *d_grad_xyz,
+                                 float *d_grad_w, float *d_grad_logh, void *stream)
+{
+    return guarded([&] {
+        if (!r || !cams || n_views < 1 || !d_grad_images) fail(GBLOD_ERR_INVALID_ARG, "bad arguments");
+        if (n > 0 && (!d_xyz || !d_w || !d_logh || !d_grad_xyz || !d_grad_w || !d_grad_logh))
+            fail(GBLOD_ERR_INVALID_ARG, "point and gradient arrays must not be NULL");
+        const gblod_render_params p = check_params(params);
+        for (int i = 0; i < n_views; ++i) check_camera(&cams[i]);
+        diff_pass(r, d_xyz, d_w, d_logh, n, cams, n_views, p, nullptr, d_grad_images, d_grad_xyz, d_grad_w,
+                  d_grad_logh, (cudaStream_t)stream);
     });
 }
 

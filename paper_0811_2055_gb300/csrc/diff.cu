@@ -1,0 +1,319 @@
+// Differentiable float splat: forward image and its adjoint with respect to the points'
+// positions, weights and log smoothing lengths, for fitting a node's representatives to the
+// full-data image (the paper's goal that the LOD image be indistinguishable from a full render).
+//
+// Reading (float path, not the exact integer path): fp32 projection as in the renderer,
+// sigma = clamp(F exp(l) / zc, sigma_min, sigma_max), kernel
+//   K(r) = (exp(-r^2 / 2 sigma^2) - exp(-4.5)) / (2 pi sigma^2 C'),  r < 3 sigma,  C' = 1 - 5.5 e^-4.5
+// (unit integral, continuous at the support edge), I = sum_i w_i K_i, fp32 accumulation.
+// The adjoint recomputes every per-pixel term tile by tile; nothing is stored per pixel.
+#include <cmath>
+#include <vector>
+
+#include "render.cuh"
+
+namespace gb {
+namespace {
+
+constexpr int DT = 16;           // 16 x 16 tiles, one thread per pixel
+constexpr int DRT = DT * DT;     // 256 threads
+constexpr uint32_t DITEM = 1024; // records per work item
+constexpr float E45 = 0.011108996538242306f;   // exp(-4.5)
+constexpr float INV_2PI_C = 0.16951204f;       // 1 / (2 pi (1 - 5.5 exp(-4.5)))
+
+struct DCam {
+    float ex, ey, ez, rx, ry, rz, ux, uy, uz, fx, fy, fz;
+    float F, CX, CY, ZN, smin, smax;
+    int W, H, tiles_x, tiles_y;
+};
+
+struct DRec {
+    uint32_t idx;
+    float u, v, s;
+};
+
+struct DProj {
+    float u, v, s, xc, yc, zc;
+    bool clamped;
+};
+
+__device__ __forceinline__ bool dproject(const DCam &c, const float *xyz, const float *logh, uint32_t i, DProj &o)
+{
+    const float dx = xyz[3 * i] - c.ex, dy = xyz[3 * i + 1] - c.ey, dz = xyz[3 * i + 2] - c.ez;
+    o.xc = c.rx * dx + c.ry * dy + c.rz * dz;
+    o.yc = c.ux * dx + c.uy * dy + c.uz * dz;
+    o.zc = c.fx * dx + c.fy * dy + c.fz * dz;
+    if (!(o.zc > c.ZN)) return false;
+    const float iz = 1.0f / o.zc;
+    o.u = c.CX + c.F * o.xc * iz;
+    o.v = c.CY - c.F * o.yc * iz;
+    const float s = c.F * expf(logh[i]) * iz;
+    o.clamped = !(s >= c.smin && s <= c.smax);
+    o.s = s >= c.smin ? (s <= c.smax ? s : c.smax) : c.smin;
+    const float R = 3.0f * o.s + 1.0f;
+    return o.u + R >= 0.0f && o.u - R <= (float)c.W && o.v + R >= 0.0f && o.v - R <= (float)c.H;
+}
+
+__device__ __forceinline__ void dtiles(const DCam &c, const DProj &o, int &tx0, int &tx1, int &ty0, int &ty1)
+{
+    const float R = 3.0f * o.s + 1.0f;
+    const int x0 = max(0, (int)floorf(o.u - R - 0.5f)), x1 = min(c.W - 1, (int)ceilf(o.u + R - 0.5f));
+    const int y0 = max(0, (int)floorf(o.v - R - 0.5f)), y1 = min(c.H - 1, (int)ceilf(o.v + R - 0.5f));
+    tx0 = x0 / DT;
+    tx1 = x1 / DT;
+    ty0 = y0 / DT;
+    ty1 = y1 / DT;
+    if (x0 > x1 || y0 > y1) tx0 = 1, tx1 = 0;
+}
+
+// count (SCATTER = false) or write (SCATTER = true) the (tile, point) records of views [v0, v0 + nv)
+template <bool SCATTER>
+__global__ void __launch_bounds__(256) k_dbin(const DCam *__restrict__ cams, int v0, int nv, const float *xyz,
+                                             const float *logh, uint32_t n, uint32_t *cnt_or_cursor, DRec *rec)
+{
+    const DCam &c0 = cams[v0];
+    const uint32_t ntiles = (uint32_t)(c0.tiles_x * c0.tiles_y);
+    const unsigned long long total = (unsigned long long)nv * n;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = gbd::lanemask_lt();
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         e - threadIdx.x < total; e += (unsigned long long)gridDim.x * blockDim.x) {
+        DProj o;
+        bool vis = false;
+        int vl = 0;
+        uint32_t i = 0;
+        if (e < total) {
+            vl = (int)(e / n);
+            i = (uint32_t)(e % n);
+            vis = dproject(cams[v0 + vl], xyz, logh, i, o);
+        }
+        if (vis) {
+            int tx0, tx1, ty0, ty1;
+            dtiles(cams[v0 + vl], o, tx0, tx1, ty0, ty1);
+            const int tilesx = cams[v0 + vl].tiles_x;
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) {
+                    const uint32_t t = (uint32_t)vl * ntiles + (uint32_t)(ty * tilesx + tx);
+                    const uint32_t mask = __activemask();
+                    const uint32_t peers = __match_any_sync(mask, t);
+                    const int leader = __ffs(peers) - 1;
+                    if (!SCATTER) {
+                        if (lane == leader) atomicAdd(&cnt_or_cursor[t], (uint32_t)__popc(peers));
+                    } else {
+                        uint32_t b = 0;
+                        if (lane == leader) b = atomicAdd(&cnt_or_cursor[t], (uint32_t)__popc(peers));
+                        b = __shfl_sync(peers, b, leader);
+                        rec[b + __popc(peers & lt)] = DRec{i, o.u, o.v, o.s};
+                    }
+                }
+        }
+    }
+}
+
+__global__ void k_ditems(uint32_t ntiles_all, const uint32_t *cnt, uint32_t *icnt)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles_all) icnt[t] = (cnt[t] + DITEM - 1) / DITEM;
+}
+
+__global__ void k_dfill(uint32_t ntiles_all, const uint32_t *cnt, const uint32_t *off, const uint32_t *ioff,
+                        uint4 *items)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles_all) return;
+    uint32_t k = ioff[t];
+    for (uint32_t s = 0; s < cnt[t]; s += DITEM, ++k) items[k] = make_uint4(t, off[t] + s, off[t] + min(cnt[t], s + DITEM), 0u);
+}
+
+__global__ void __launch_bounds__(DRT) k_dforward(const DCam *__restrict__ cams, int v0, const DRec *__restrict__ rec,
+                                                  const uint4 *__restrict__ items, const float *__restrict__ w,
+                                                  float *images)
+{
+    __shared__ float4 sR[DRT];
+    __shared__ float sW[DRT];
+    const uint4 it = items[blockIdx.x];
+    const DCam &c = cams[v0];
+    const uint32_t ntiles = (uint32_t)(c.tiles_x * c.tiles_y);
+    const uint32_t vl = it.x / ntiles, t = it.x % ntiles;
+    const int px = (int)(t % c.tiles_x) * DT + (threadIdx.x % DT), py = (int)(t / c.tiles_x) * DT + (threadIdx.x / DT);
+    const float fx = px + 0.5f, fy = py + 0.5f;
+    float acc = 0.0f;
+    for (uint32_t b = it.y; b < it.z; b += DRT) {
+        __syncthreads();
+        if (b + threadIdx.x < it.z) {
+            const DRec r = rec[b + threadIdx.x];
+            sR[threadIdx.x] = make_float4(r.u, r.v, r.s, 0.0f);
+            sW[threadIdx.x] = w[r.idx];
+        }
+        __syncthreads();
+        const int nb = (int)min((uint32_t)DRT, it.z - b);
+        for (int j = 0; j < nb; ++j) {
+            const float4 q = sR[j];
+            const float dx = fx - q.x, dy = fy - q.y, r2 = dx * dx + dy * dy, s2 = q.z * q.z;
+            if (r2 < 9.0f * s2) acc += sW[j] * (expf(-r2 / (2.0f * s2)) - E45) * (INV_2PI_C / s2);
+        }
+    }
+    if (px < c.W && py < c.H && acc != 0.0f)
+        atomicAdd(&images[((size_t)(v0 + vl) * c.H + py) * c.W + px], acc);
+}
+
+__global__ void __launch_bounds__(DRT) k_dbackward(const DCam *__restrict__ cams, int v0, const DRec *__restrict__ rec,
+                                                   const uint4 *__restrict__ items, const float *__restrict__ xyz,
+                                                   const float *__restrict__ w, const float *__restrict__ logh,
+                                                   const float *__restrict__ grad_img, float *gxyz, float *gw,
+                                                   float *glogh)
+{
+    __shared__ float4 sR[DRT];
+    __shared__ uint32_t sI[DRT];
+    __shared__ float4 part[DRT / 32][DRT]; // per warp, per record: dw, du, dv, ds
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint4 it = items[blockIdx.x];
+    const DCam &c0 = cams[v0];
+    const uint32_t ntiles = (uint32_t)(c0.tiles_x * c0.tiles_y);
+    const uint32_t vl = it.x / ntiles, t = it.x % ntiles;
+    const DCam &c = cams[v0 + vl];
+    const int px = (int)(t % c.tiles_x) * DT + (threadIdx.x % DT), py = (int)(t / c.tiles_x) * DT + (threadIdx.x / DT);
+    const bool inside = px < c.W && py < c.H;
+    const float g = inside ? grad_img[((size_t)(v0 + vl) * c.H + py) * c.W + px] : 0.0f;
+    const float fx = px + 0.5f, fy = py + 0.5f;
+    for (uint32_t b = it.y; b < it.z; b += DRT) {
+        __syncthreads();
+        if (b + threadIdx.x < it.z) {
+            const DRec r = rec[b + threadIdx.x];
+            sR[threadIdx.x] = make_float4(r.u, r.v, r.s, w[r.idx]);
+            sI[threadIdx.x] = r.idx;
+        }
+        __syncthreads();
+        const int nb = (int)min((uint32_t)DRT, it.z - b);
+        for (int j = 0; j < nb; ++j) {
+            const float4 q = sR[j];
+            const float dx = fx - q.x, dy = fy - q.y, r2 = dx * dx + dy * dy, s = q.z, s2 = s * s;
+            float tw = 0.f, tu = 0.f, tv = 0.f, ts = 0.f;
+            if (g != 0.0f && r2 < 9.0f * s2) {
+                const float e = expf(-r2 / (2.0f * s2)) * (INV_2PI_C / s2);
+                const float k = e - E45 * (INV_2PI_C / s2);
+                const float gwv = g * q.w;
+                tw = g * k;
+                tu = gwv * e * dx / s2;
+                tv = gwv * e * dy / s2;
+                ts = gwv * (e * r2 / (s2 * s) - 2.0f * k / s);
+            }
+            for (int d = 16; d > 0; d >>= 1) {
+                tw += __shfl_xor_sync(0xffffffffu, tw, d);
+                tu += __shfl_xor_sync(0xffffffffu, tu, d);
+                tv += __shfl_xor_sync(0xffffffffu, tv, d);
+                ts += __shfl_xor_sync(0xffffffffu, ts, d);
+            }
+            if (lane == 0) part[warp][j] = make_float4(tw, tu, tv, ts);
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < nb) {
+            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < DRT / 32; ++k) {
+                const float4 p = part[k][threadIdx.x];
+                sum.x += p.x; sum.y += p.y; sum.z += p.z; sum.w += p.w;
+            }
+            if (sum.x != 0.f || sum.y != 0.f || sum.z != 0.f || sum.w != 0.f) {
+                const uint32_t i = sI[threadIdx.x];
+                DProj o;
+                dproject(c, xyz, logh, i, o);
+                const float iz = 1.0f / o.zc;
+                const float du = sum.y, dv = sum.z, ds = sum.w;
+                const float dxc = du * c.F * iz;
+                const float dyc = -dv * c.F * iz;
+                const float ds_dz = o.clamped ? 0.0f : -o.s * iz;
+                const float dzc = du * (-c.F * o.xc * iz * iz) + dv * (c.F * o.yc * iz * iz) + ds * ds_dz;
+                atomicAdd(&gxyz[3 * i], c.rx * dxc + c.ux * dyc + c.fx * dzc);
+                atomicAdd(&gxyz[3 * i + 1], c.ry * dxc + c.uy * dyc + c.fy * dzc);
+                atomicAdd(&gxyz[3 * i + 2], c.rz * dxc + c.uz * dyc + c.fz * dzc);
+                atomicAdd(&gw[i], sum.x);
+                if (!o.clamped) atomicAdd(&glogh[i], ds * o.s);
+            }
+        }
+    }
+}
+
+DCam make_dcam(const gblod_camera &c, const gblod_render_params &rp)
+{
+    DCam d;
+    d.ex = (float)c.eye[0]; d.ey = (float)c.eye[1]; d.ez = (float)c.eye[2];
+    d.rx = (float)c.right[0]; d.ry = (float)c.right[1]; d.rz = (float)c.right[2];
+    d.ux = (float)c.up[0]; d.uy = (float)c.up[1]; d.uz = (float)c.up[2];
+    d.fx = (float)c.fwd[0]; d.fy = (float)c.fwd[1]; d.fz = (float)c.fwd[2];
+    d.F = (float)c.f_px; d.CX = (float)c.cx; d.CY = (float)c.cy; d.ZN = (float)c.z_near;
+    d.smin = (float)rp.sigma_min_px;
+    d.smax = (float)rp.sigma_max_px;
+    d.W = c.width;
+    d.H = c.height;
+    d.tiles_x = (c.width + DT - 1) / DT;
+    d.tiles_y = (c.height + DT - 1) / DT;
+    return d;
+}
+
+} // namespace
+
+// Runs forward (grad_img == nullptr) or backward over chunks of views whose records fit a budget.
+void diff_pass(gblod_renderer *r, const float *xyz, const float *w, const float *logh, uint64_t n,
+               const gblod_camera *cams, int nv, const gblod_render_params &rp, float *images, const float *grad_img,
+               float *gxyz, float *gw, float *glogh, cudaStream_t s)
+{
+    if (n >= 0xFFFFFFFFull) fail(GBLOD_ERR_INVALID_ARG, "too many points");
+    const int W = cams[0].width, H = cams[0].height;
+    for (int v = 0; v < nv; ++v)
+        if (cams[v].width != W || cams[v].height != H) fail(GBLOD_ERR_INVALID_ARG, "all views need one resolution");
+    const Allocator &A = r->A;
+    std::vector<DCam> hc(nv);
+    for (int v = 0; v < nv; ++v) hc[v] = make_dcam(cams[v], rp);
+    r->d_cams.ensure(A, (size_t)nv * sizeof(DCam), s);
+    DCam *dc = reinterpret_cast<DCam *>(r->d_cams.p);
+    GB_CUDA(cudaMemcpyAsync(dc, hc.data(), (size_t)nv * sizeof(DCam), cudaMemcpyHostToDevice, s));
+    const size_t npix = (size_t)W * H;
+    if (images) GB_CUDA(cudaMemsetAsync(images, 0, (size_t)nv * npix * sizeof(float), s));
+    if (grad_img) {
+        GB_CUDA(cudaMemsetAsync(gxyz, 0, n * 3 * sizeof(float), s));
+        GB_CUDA(cudaMemsetAsync(gw, 0, n * sizeof(float), s));
+        GB_CUDA(cudaMemsetAsync(glogh, 0, n * sizeof(float), s));
+    }
+    if (n == 0) return;
+    const uint32_t ntiles = (uint32_t)(hc[0].tiles_x * hc[0].tiles_y);
+    const unsigned G = (unsigned)persistent_blocks(4);
+    // views per chunk: about 2^26 (view, point) pairs, so records stay near a few GB
+    const int vchunk = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)nv, (1ull << 26) / std::max<uint64_t>(n, 1)));
+    for (int v0 = 0; v0 < nv; v0 += vchunk) {
+        const int cnv = std::min(vchunk, nv - v0);
+        const uint32_t nt = ntiles * (uint32_t)cnv;
+        r->d_cnt.ensure(A, nt, s);
+        r->d_off.ensure(A, nt + 1, s);
+        r->d_cur.ensure(A, nt, s);
+        r->d_icnt.ensure(A, nt, s);
+        r->d_ioff.ensure(A, nt + 1, s);
+        GB_CUDA(cudaMemsetAsync(r->d_cnt.p, 0, (size_t)nt * 4, s));
+        launch(GBLOD_K_RENDER_OTHER, k_dbin<false>, dim3(G), dim3(256), 0, s, (const DCam *)dc, v0, cnv, xyz, logh,
+               (uint32_t)n, r->d_cnt.p, (DRec *)nullptr);
+        scan_exclusive_u32(A, r->scan, r->d_cnt.p, r->d_off.p, nt, r->d_off.p + nt, s);
+        launch(GBLOD_K_RENDER_OTHER, k_ditems, dim3((nt + 255) / 256), dim3(256), 0, s, nt, (const uint32_t *)r->d_cnt.p,
+               r->d_icnt.p);
+        scan_exclusive_u32(A, r->scan, r->d_icnt.p, r->d_ioff.p, nt, r->d_ioff.p + nt, s);
+        uint32_t tot[2];
+        GB_CUDA(cudaMemcpyAsync(&tot[0], r->d_off.p + nt, 4, cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaMemcpyAsync(&tot[1], r->d_ioff.p + nt, 4, cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        r->d_rec.ensure(A, (size_t)tot[0] * sizeof(DRec), s);
+        r->d_items.ensure(A, tot[1], s);
+        GB_CUDA(cudaMemcpyAsync(r->d_cur.p, r->d_off.p, (size_t)nt * 4, cudaMemcpyDeviceToDevice, s));
+        DRec *rec = reinterpret_cast<DRec *>(r->d_rec.p);
+        launch(GBLOD_K_RENDER_OTHER, k_dbin<true>, dim3(G), dim3(256), 0, s, (const DCam *)dc, v0, cnv, xyz, logh,
+               (uint32_t)n, r->d_cur.p, rec);
+        launch(GBLOD_K_RENDER_OTHER, k_dfill, dim3((nt + 255) / 256), dim3(256), 0, s, nt, (const uint32_t *)r->d_cnt.p,
+               (const uint32_t *)r->d_off.p, (const uint32_t *)r->d_ioff.p, r->d_items.p);
+        if (!grad_img)
+            launch(GBLOD_K_SPLAT, k_dforward, dim3(tot[1]), dim3(DRT), 0, s, (const DCam *)dc, v0, (const DRec *)rec,
+                   (const uint4 *)r->d_items.p, w, images);
+        else
+            launch(GBLOD_K_SPLAT, k_dbackward, dim3(tot[1]), dim3(DRT), 0, s, (const DCam *)dc, v0, (const DRec *)rec,
+                   (const uint4 *)r->d_items.p, xyz, w, logh, grad_img, gxyz, gw, glogh);
+    }
+}
+
+} // namespace gb

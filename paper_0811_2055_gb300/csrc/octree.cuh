@@ -23,6 +23,12 @@ struct gblod_octree {
     uint32_t *sidx = nullptr;    // n: input index per sorted position
     std::vector<uint64_t> level_first; // host: first node index of every depth, plus the end
     size_t bytes = 0;
+    // 16-bit block codes (gblod_octree_quantize); null until coded
+    ushort4 *q4 = nullptr;      // n_points: position codes x, y, z and the h code
+    uint16_t *qw = nullptr;     // n_points: weight code
+    float4 *qa = nullptr;       // 2 per node: (qlo x, y, z, qstep), (w lo, w step, h lo, h step)
+    gblod_node *qnodes = nullptr; // node table with bounds and h_cull of the decoded subtrees
+    bool has_float = true, has_block16 = false;
 };
 
 namespace gb {
@@ -30,6 +36,28 @@ namespace gb {
 gblod_octree *build_octree(const float *xyz, const float *mass, const float *h, const uint32_t *ids, uint64_t n,
                            const gblod_build_params &p, const Allocator &A, cudaStream_t s);
 void free_octree(gblod_octree *o);
+
+// Codes every stored point (16-bit block codes); GBLOD_QUANTIZE_DROP_FLOAT frees the fp32 points.
+void block_quantize(gblod_octree *o, uint32_t flags, cudaStream_t s);
+
+// Decoding of the 16-bit block codes: one IEEE round-to-nearest per operation, no FMA.
+__device__ __forceinline__ float block_decode_pos(uint32_t c, float lo, float step)
+{
+    return __fadd_rn(lo, __fmul_rn(__fadd_rn(__uint2float_rn(c), 0.5f), step));
+}
+__device__ __forceinline__ float block_decode_lin(uint32_t c, float lo, float step)
+{
+    return __fadd_rn(lo, __fmul_rn(__uint2float_rn(c), step));
+}
+__device__ __forceinline__ void block_decode(const ushort4 q, uint32_t cw, const float4 A, const float4 B, float &x,
+                                             float &y, float &z, float &w, float &h)
+{
+    x = block_decode_pos(q.x, A.x, A.w);
+    y = block_decode_pos(q.y, A.y, A.w);
+    z = block_decode_pos(q.z, A.z, A.w);
+    w = block_decode_lin(cw, B.x, B.y);
+    h = block_decode_lin(q.w, B.z, B.w);
+}
 
 // Work arrays the subselection reads and writes (all device pointers).
 struct SelectIn {

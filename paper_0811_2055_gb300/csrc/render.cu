@@ -20,6 +20,7 @@
 namespace gb {
 
 void check_image(const gblod_camera &c);
+void check_format(const gblod_octree *o, const gblod_render_params &rp);
 
 // integer kernel tables (Gaussian, cubic), filled once per device
 __device__ int32_t g_ktab[2][1024];
@@ -342,6 +343,14 @@ struct SrcLOD {
     const unsigned long long *total;
 };
 
+// selected nodes' 16-bit block codes (decoded on load)
+struct SrcLODQ : SrcLOD {
+    const ushort4 *q4;
+    const uint16_t *qw;
+    const float4 *qa;
+    const uint32_t *sel; // node index per selected entry
+};
+
 struct SrcFlat {
     const float *xyz, *mass, *h;
     unsigned long long n;
@@ -393,6 +402,21 @@ __device__ __forceinline__ void src_load(const SrcLOD &s, unsigned long long e, 
     const float4 q = s.pts4[p];
     x = q.x; y = q.y; z = q.z; w = q.w;
     h = s.hs[p];
+}
+__device__ __forceinline__ void src_load(const SrcLODQ &s, unsigned long long e, uint32_t j0, uint32_t j1, float &x,
+                                         float &y, float &z, float &w, float &h)
+{
+    uint32_t lo = j0, hi = j1 + 1;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s.pfx[mid] <= e)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const unsigned long long p = (unsigned long long)((long long)e + s.base[lo]);
+    const uint32_t node = s.sel[lo];
+    block_decode(s.q4[p], s.qw[p], s.qa[2 * node], s.qa[2 * node + 1], x, y, z, w, h);
 }
 __device__ __forceinline__ void src_load(const SrcFlat &s, unsigned long long e, uint32_t, uint32_t, float &x,
                                          float &y, float &z, float &w, float &h)
@@ -539,9 +563,14 @@ struct SplatSmem {
     int32_t K[1024];
     int4 A[RT];                             // U, V, S, Wh = Wq >> 16
     uint4 B[RT];                            // QL low, QL high, Wl = Wq & 0xFFFF, unused
-    uint32_t box[RT];                       // tile-local box x0 | x1 << 8 | y0 << 16 | y1 << 24
-    uint8_t list[RT / 32][SPLAT_SLOTS][RT]; // per warp and block: records touching it
+    uint8_t list[RT / 32][SPLAT_SLOTS][RT]; // per warp and block: small records from the front,
+                                            // large ones from the back
 };
+
+// A record is "small" when QL <= 2^30: every pixel of a block its support reaches then lies
+// within 2^15 + 8 px of its centre on each axis (in 1/256 px), so dx^2 + dy^2 < 2^32 and the
+// table index (q S) >> 37 is the high word of a 32 x 32 product shifted by 5.
+constexpr unsigned long long QL_SMALL = 1ull << 30;
 
 // Splats records [it.y, it.z) of tile `tile` (index inside the view) of view P into img.
 __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const uint4 it, const uint32_t tile,
@@ -570,16 +599,6 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
             const unsigned long long QL = 140737488355327ull / (unsigned long long)R.z + 1ull;
             sm.A[threadIdx.x] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)(Wq >> 16));
             sm.B[threadIdx.x] = make_uint4((uint32_t)QL, (uint32_t)(QL >> 32), (uint32_t)(Wq & 0xFFFFull), 0u);
-            int x0, x1, y0, y1;
-            splat_box((int)R.x, (int)R.y, R.z, P.W, P.H, x0, x1, y0, y1);
-            x0 = max(x0 - X0, 0);
-            x1 = min(x1 - X0, TWc - 1);
-            y0 = max(y0 - Y0, 0);
-            y1 = min(y1 - Y0, THc - 1);
-            // an empty box touches no block: encode it with y0 = 255 > y1 = 0
-            sm.box[threadIdx.x] = x0 <= x1 && y0 <= y1
-                                      ? (uint32_t)x0 | (uint32_t)x1 << 8 | (uint32_t)y0 << 16 | (uint32_t)y1 << 24
-                                      : 0x00FF0000u;
         }
         __syncthreads();
 #pragma unroll
@@ -588,42 +607,71 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
             if (b >= nblk) break; // warp-uniform
             const int bx0 = (b % nbx) * 8, by0 = (b / nbx) * 4;
             if (bx0 >= TWc || by0 >= THc) continue;
-            // records whose box touches this warp's block k
-            int cnt = 0;
+            // records whose support reaches a pixel centre of this block (exact test q_min < QL
+            // against the nearest point of the block's pixel-centre rectangle)
+            const int cx0 = (X0 + bx0) * 256 + 128, cx1 = (X0 + min(bx0 + 7, TWc - 1)) * 256 + 128;
+            const int cy0 = (Y0 + by0) * 256 + 128, cy1 = (Y0 + min(by0 + 3, THc - 1)) * 256 + 128;
+            uint8_t *lst = sm.list[warp][k];
+            int ns = 0, nl = 0;
             for (int j0 = 0; j0 < nb; j0 += 32) {
                 const int j = j0 + lane;
-                bool touch = false;
+                bool ts = false, tl = false;
                 if (j < nb) {
-                    const uint32_t bx = sm.box[j];
-                    const int x0 = bx & 255, x1 = (bx >> 8) & 255, y0 = (bx >> 16) & 255, y1 = bx >> 24;
-                    touch = x0 <= bx0 + 7 && x1 >= bx0 && y0 <= by0 + 3 && y1 >= by0 && y0 <= y1;
+                    const int4 A = sm.A[j];
+                    const uint4 B = sm.B[j];
+                    const long long ex = (long long)A.x - (long long)min(max(A.x, cx0), cx1);
+                    const long long ey = (long long)A.y - (long long)min(max(A.y, cy0), cy1);
+                    const unsigned long long qm = (unsigned long long)(ex * ex + ey * ey);
+                    const unsigned long long QL = ((unsigned long long)B.y << 32) | B.x;
+                    const bool touch = qm < QL;
+                    const bool small = QL <= QL_SMALL;
+                    ts = touch && small;
+                    tl = touch && !small;
                 }
-                const uint32_t m = __ballot_sync(0xffffffffu, touch);
-                if (touch) sm.list[warp][k][cnt + __popc(m & lt)] = (uint8_t)j;
-                cnt += __popc(m);
+                const uint32_t ms = __ballot_sync(0xffffffffu, ts), ml = __ballot_sync(0xffffffffu, tl);
+                if (ts) lst[ns + __popc(ms & lt)] = (uint8_t)j;
+                if (tl) lst[RT - 1 - (nl + __popc(ml & lt))] = (uint8_t)j;
+                ns += __popc(ms);
+                nl += __popc(ml);
             }
             __syncwarp();
             const int pxl = bx0 + (lane & 7), pyl = by0 + (lane >> 3);
-            const bool pv = pxl < TWc && pyl < THc;
             const int pxv = (X0 + pxl) * 256 + 128, pyv = (Y0 + pyl) * 256 + 128;
             unsigned long long a = acc[k];
             uint32_t al = acc_lo[k];
-#pragma unroll 2
-            for (int i = 0; i < cnt; ++i) {
-                const int j = sm.list[warp][k][i];
+            unsigned hk = 0;
+            // lanes whose pixel lies outside the tile compute too; their sums are never stored
+#pragma unroll 4
+            for (int i = 0; i < ns; ++i) {
+                const int j = lst[i];
+                const int4 A = sm.A[j];
+                const uint2 B = make_uint2(sm.B[j].x, sm.B[j].z);
+                const int dx = pxv - A.x, dy = pyv - A.y;
+                const uint32_t q = (uint32_t)(dx * dx) + (uint32_t)(dy * dy);
+                if (q < B.x) {
+                    const uint32_t idx = __umulhi(q, (uint32_t)A.z) >> 5;
+                    const uint32_t kv = (uint32_t)sm.K[idx];
+                    a += (unsigned long long)(uint32_t)A.w * kv;
+                    al += (B.y * kv) >> 16;
+                    ++hk;
+                }
+            }
+            for (int i = RT - nl; i < RT; ++i) {
+                const int j = lst[i];
                 const int4 A = sm.A[j];
                 const uint4 B = sm.B[j];
                 const int dx = pxv - A.x, dy = pyv - A.y;
                 const unsigned long long q = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
                 const unsigned long long QL = ((unsigned long long)B.y << 32) | B.x;
-                if (q < QL && pv) {
+                if (q < QL) {
                     const uint32_t idx = (uint32_t)((q * (unsigned long long)(uint32_t)A.z) >> 37);
                     const uint32_t kv = (uint32_t)sm.K[idx];
                     a += (unsigned long long)(uint32_t)A.w * kv;
                     al += (B.z * kv) >> 16;
-                    ++hits;
+                    ++hk;
                 }
             }
+            if (pxl < TWc && pyl < THc) hits += hk;
             acc[k] = a;
             acc_lo[k] = al;
         }
@@ -865,6 +913,9 @@ struct ViewDev {
     const gblod_node *nodes;
     const float4 *pts4;
     const float *hs;
+    const ushort4 *q4;   // non-null: draw the 16-bit block codes
+    const uint16_t *qw;
+    const float4 *qa;
     unsigned long long *accum;
     uint8_t *image;
     unsigned long long pix_base;
@@ -883,17 +934,12 @@ __global__ void k_set_views(ViewChunk c, ViewDev *dst)
     for (int i = threadIdx.x; i < c.n; i += blockDim.x) dst[c.first + i] = c.v[i];
 }
 
-__global__ void k_bzero(const ViewDev *__restrict__ views, int n, unsigned long long total)
+__global__ void k_bzero(const ViewDev *__restrict__ views)
 {
-    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (unsigned long long)gridDim.x * blockDim.x) {
-        int lo = 0, hi = n;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (views[mid].pix_base <= e) lo = mid; else hi = mid;
-        }
-        views[lo].accum[e - views[lo].pix_base] = 0ull;
-    }
+    const ViewDev &V = views[blockIdx.y];
+    const size_t n = (size_t)V.P.W * V.P.H;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        V.accum[i] = 0ull;
 }
 
 __global__ void k_bselect_init(const ViewDev *__restrict__ views, int n, unsigned long long *front, uint32_t *cnt)
@@ -1011,11 +1057,18 @@ __device__ __forceinline__ int bsrc_load(const SrcBatch &s, unsigned long long e
         const uint32_t mid = (lo + hi) >> 1;
         if (s.pfx[mid] <= e) lo = mid; else hi = mid;
     }
-    const int v = (int)(s.sel[lo] >> 32);
+    const unsigned long long ent = s.sel[lo];
+    const int v = (int)(ent >> 32);
     const unsigned long long p = (unsigned long long)((long long)e + s.base[lo]);
-    const float4 q = s.views[v].pts4[p];
-    x = q.x; y = q.y; z = q.z; w = q.w;
-    h = s.views[v].hs[p];
+    const ViewDev &V = s.views[v];
+    if (V.q4) {
+        const uint32_t node = (uint32_t)ent;
+        block_decode(V.q4[p], V.qw[p], V.qa[2 * node], V.qa[2 * node + 1], x, y, z, w, h);
+    } else {
+        const float4 q = V.pts4[p];
+        x = q.x; y = q.y; z = q.z; w = q.w;
+        h = V.hs[p];
+    }
     return v;
 }
 
@@ -1028,11 +1081,20 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
     const int lane = threadIdx.x & 31;
     const uint32_t lt = gbd::lanemask_lt();
     unsigned long long splats = 0, pairs = 0;
+    __shared__ Proj sP[2];
+    __shared__ int sV[2];
     for (unsigned long long a = (unsigned long long)blockIdx.x * CHUNK; a < total;
          a += (unsigned long long)gridDim.x * CHUNK) {
         const unsigned long long b = min(total, a + CHUNK);
         uint32_t j0, j1;
         bsrc_range(src, a, b, j0, j1);
+        // the chunk's points belong to the views of its first and last nodes, or rarely in between
+        if (threadIdx.x < 2) {
+            const int vv = (int)(src.sel[threadIdx.x == 0 ? j0 : j1] >> 32);
+            sV[threadIdx.x] = vv;
+            sP[threadIdx.x] = src.views[vv].P;
+        }
+        __syncthreads();
         for (unsigned long long e0 = a; e0 < b; e0 += RT) {
             const unsigned long long e = e0 + threadIdx.x;
             int res = 0, v = 0;
@@ -1040,7 +1102,8 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
             if (e < b) {
                 float x, y, z, w, h;
                 v = bsrc_load(src, e, j0, j1, x, y, z, w, h);
-                res = project(src.views[v].P, x, y, z, w, h, s);
+                const Proj &Pv = v == sV[0] ? sP[0] : (v == sV[1] ? sP[1] : src.views[v].P);
+                res = project(Pv, x, y, z, w, h, s);
             }
             if (!SCATTER) {
                 if (__any_sync(0xffffffffu, res < 0) && lane == 0) atomicOr(status, ST_RANGE);
@@ -1052,7 +1115,7 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
                 }
             }
             if (res == 1) {
-                const Proj &P = src.views[v].P;
+                const Proj &P = v == sV[0] ? sP[0] : (v == sV[1] ? sP[1] : src.views[v].P);
                 const uint32_t tb = src.views[v].tile_base;
                 if (!SCATTER) ++splats;
                 int x0, x1, y0, y1;
@@ -1080,6 +1143,7 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
                 }
             }
         }
+        __syncthreads();
     }
     if (!SCATTER) {
         for (int d = 16; d > 0; d >>= 1) {
@@ -1117,16 +1181,22 @@ __global__ void k_bfill_items(uint32_t ntiles, const ViewDev *__restrict__ views
 
 __global__ void __launch_bounds__(RT, 4) k_bsplat(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
                                                   const uint32_t *nitems_p, uint32_t items_cap,
-                                                  const ViewDev *__restrict__ views, FrameStatsDev *stats)
+                                                  const ViewDev *__restrict__ views, unsigned *next_item,
+                                                  FrameStatsDev *stats)
 {
     __shared__ SplatSmem sm;
     __shared__ Proj sP;
+    __shared__ uint32_t s_item;
     int kernel_loaded = -1;
     unsigned hits = 0;
     const uint32_t nitems = min(*nitems_p, items_cap);
-    for (uint32_t i = blockIdx.x; i < nitems; i += gridDim.x) {
-        const uint4 it = items[i];
+    for (;;) {
         __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(next_item, 1u);
+        __syncthreads();
+        const uint32_t i = s_item;
+        if (i >= nitems) break;
+        const uint4 it = items[i];
         if (threadIdx.x == 0) sP = views[it.w].P;
         __syncthreads();
         const Proj P = sP;
@@ -1139,46 +1209,51 @@ __global__ void __launch_bounds__(RT, 4) k_bsplat(const uint4 *__restrict__ rec,
     count_hits(hits, stats);
 }
 
-__global__ void k_bmax(const ViewDev *__restrict__ views, int n, unsigned long long total, unsigned long long *maxv)
+// R4 over the views of a batch: blockIdx.y = view, grid-stride over that view's pixels
+__global__ void k_bmax(const ViewDev *__restrict__ views, unsigned long long *maxv)
 {
-    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (unsigned long long)gridDim.x * blockDim.x) {
-        int lo = 0, hi = n;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (views[mid].pix_base <= e) lo = mid; else hi = mid;
-        }
-        const unsigned long long a = views[lo].accum[e - views[lo].pix_base];
-        if (a) atomicMax(&maxv[lo], a);
+    const ViewDev &V = views[blockIdx.y];
+    const size_t n = (size_t)V.P.W * V.P.H;
+    unsigned long long m = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = V.accum[i] > m ? V.accum[i] : m;
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, d);
+        m = o > m ? o : m;
     }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&maxv[blockIdx.y], m);
 }
-
-__global__ void k_btonemap(const ViewDev *__restrict__ views, int n, unsigned long long total,
-                           const unsigned long long *maxv, int auto_range)
+__global__ void k_btonemap(const ViewDev *__restrict__ views, const unsigned long long *maxv, int auto_range)
 {
-    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (unsigned long long)gridDim.x * blockDim.x) {
-        int lo_v = 0, hi_v = n;
-        while (hi_v - lo_v > 1) {
-            const int mid = (lo_v + hi_v) >> 1;
-            if (views[mid].pix_base <= e) lo_v = mid; else hi_v = mid;
-        }
-        const ViewDev &V = views[lo_v];
-        if (!V.image) continue;
+    const ViewDev &V = views[blockIdx.y];
+    if (!V.image) return;
+    __shared__ double s_lo;
+    __shared__ float s_l2lo, s_scale;
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
         double hi = V.hi_acc, lo = V.lo_acc;
         if (auto_range) {
-            hi = (double)maxv[lo_v];
+            hi = (double)maxv[blockIdx.y];
             lo = hi * 1e-4;
         }
-        const unsigned long long local = e - V.pix_base;
-        const unsigned long long a = V.accum[local];
+        s_ok = (hi > 0.0 && lo > 0.0 && hi > lo) ? 1 : 0;
+        s_lo = lo;
+        s_l2lo = s_ok ? (float)log2(lo) : 0.0f;
+        s_scale = s_ok ? (float)(255.0 / log2(hi / lo)) : 0.0f;
+    }
+    __syncthreads();
+    const double lo = s_lo;
+    const float l2lo = s_l2lo, scale = s_scale;
+    const int ok = s_ok;
+    const size_t n = (size_t)V.P.W * V.P.H;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long a = V.accum[i];
         uint8_t o = 0;
-        if (hi > 0.0 && lo > 0.0 && hi > lo && (double)a > lo) {
-            const float l2lo = (float)log2(lo), scale = (float)(255.0 / log2(hi / lo));
+        if (ok && (double)a > lo) {
             const float t = rintf((log2f((float)a) - l2lo) * scale);
             o = (uint8_t)(t > 255.0f ? 255.0f : (t < 0.0f ? 0.0f : t));
         }
-        V.image[local] = o;
+        V.image[i] = o;
     }
 }
 
@@ -1191,6 +1266,7 @@ struct BatchPlan {
 
 BatchPlan plan_batch(const gblod_view *views, int n, const gblod_render_params &rp)
 {
+    if (n > 65535) fail(GBLOD_ERR_INVALID_ARG, "a batch holds at most 65535 views");
     BatchPlan b;
     b.host.resize(n);
     for (int v = 0; v < n; ++v) {
@@ -1198,13 +1274,21 @@ BatchPlan plan_batch(const gblod_view *views, int n, const gblod_render_params &
         if (!V.octree) fail(GBLOD_ERR_INVALID_ARG, "batch view has no octree");
         if (!V.d_accum) fail(GBLOD_ERR_INVALID_ARG, "batch views need d_accum");
         check_image(V.camera);
+        check_format(V.octree, rp);
         ViewDev &d = b.host[v];
         std::memset(&d, 0, sizeof(d));
         d.P = make_proj(V.camera, rp);
         d.F = make_frustum(V.camera, rp, V.octree);
-        d.nodes = V.octree->nodes;
-        d.pts4 = V.octree->pts4;
-        d.hs = V.octree->hs;
+        if (rp.point_format == GBLOD_POINTS_BLOCK16) {
+            d.nodes = V.octree->qnodes;
+            d.q4 = V.octree->q4;
+            d.qw = V.octree->qw;
+            d.qa = V.octree->qa;
+        } else {
+            d.nodes = V.octree->nodes;
+            d.pts4 = V.octree->pts4;
+            d.hs = V.octree->hs;
+        }
         d.accum = reinterpret_cast<unsigned long long *>(V.d_accum);
         d.image = V.d_image;
         d.pix_base = b.npix;
@@ -1240,7 +1324,7 @@ void reserve_batch(gblod_renderer *r, const gblod_view *views, int n, const gblo
     r->b_counts.ensure(A, b.nodes + 1, s);
     r->b_pfx.ensure(A, b.nodes + 2, s);
     r->b_base.ensure(A, b.nodes + 1, s);
-    r->lvl_cnt.ensure(A, b.max_levels + 2, s);
+    r->lvl_cnt.ensure(A, b.max_levels + 3, s);
     r->tile_cnt.ensure(A, b.ntiles, s);
     r->tile_off.ensure(A, b.ntiles + 1, s);
     r->tile_cur.ensure(A, b.ntiles, s);
@@ -1265,7 +1349,7 @@ void render_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod
     // scratch must have been reserved (no allocation here, so the call can be graph-captured)
     const uint64_t items_cap = b.ntiles + r->b_rec_cap / ITEM + 1;
     if (r->b_views.cap < (size_t)n * sizeof(ViewDev) || r->b_frontA.cap < b.nodes + 1 || r->b_sel.cap < b.nodes + 1 ||
-        r->b_pfx.cap < b.nodes + 2 || r->lvl_cnt.cap < b.max_levels + 2 || r->tile_cnt.cap < b.ntiles ||
+        r->b_pfx.cap < b.nodes + 2 || r->lvl_cnt.cap < b.max_levels + 3 || r->tile_cnt.cap < b.ntiles ||
         r->tile_off.cap < b.ntiles + 1 || r->item_off.cap < b.ntiles + 1 || r->records.cap < r->b_rec_cap ||
         r->items.cap < items_cap || r->maxv.cap < (size_t)n || r->b_rec_cap == 0)
         fail(GBLOD_ERR_INVALID_ARG, "gblod_render_batch: call gblod_renderer_reserve_batch for this batch first");
@@ -1281,9 +1365,10 @@ void render_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod
     }
     const unsigned G = (unsigned)persistent_blocks(4);
     GB_CUDA(cudaMemsetAsync(r->stats, 0, offsetof(FrameStatsDev, pixel_updates_total), s));
-    GB_CUDA(cudaMemsetAsync(r->lvl_cnt.p, 0, (size_t)(b.max_levels + 2) * 4, s));
+    GB_CUDA(cudaMemsetAsync(r->lvl_cnt.p, 0, (size_t)(b.max_levels + 3) * 4, s));
     GB_CUDA(cudaMemsetAsync(r->tile_cnt.p, 0, (size_t)b.ntiles * 4, s));
-    launch(GBLOD_K_RENDER_OTHER, k_bzero, dim3(G), dim3(256), 0, s, (const ViewDev *)dv, n, b.npix);
+    const dim3 GV((unsigned)std::max(1, (int)G / n), (unsigned)n); // (blocks per view, views)
+    launch(GBLOD_K_RENDER_OTHER, k_bzero, GV, dim3(256), 0, s, (const ViewDev *)dv);
     // R1 over (view, node) pairs
     uint32_t *nsel = r->lvl_cnt.p + b.max_levels + 1;
     unsigned long long *fin = r->b_frontA.p, *fout = r->b_frontB.p;
@@ -1320,13 +1405,14 @@ void render_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod
            (const FrameStatsDev *)r->stats, r->status);
     // R3: persistent over the items of all views
     launch(GBLOD_K_SPLAT, k_bsplat, dim3(G), dim3(RT), 0, s, (const uint4 *)r->records.p, (const uint4 *)r->items.p,
-           (const uint32_t *)(r->item_off.p + b.ntiles), (uint32_t)items_cap, (const ViewDev *)dv, r->stats);
+           (const uint32_t *)(r->item_off.p + b.ntiles), (uint32_t)items_cap, (const ViewDev *)dv,
+           r->lvl_cnt.p + b.max_levels + 2, r->stats);
     // R4
     if (rp.tone_auto) {
         GB_CUDA(cudaMemsetAsync(r->maxv.p, 0, (size_t)n * 8, s));
-        launch(GBLOD_K_TONEMAP, k_bmax, dim3(G), dim3(256), 0, s, (const ViewDev *)dv, n, b.npix, r->maxv.p);
+        launch(GBLOD_K_TONEMAP, k_bmax, GV, dim3(256), 0, s, (const ViewDev *)dv, r->maxv.p);
     }
-    launch(GBLOD_K_TONEMAP, k_btonemap, dim3(G), dim3(256), 0, s, (const ViewDev *)dv, n, b.npix,
+    launch(GBLOD_K_TONEMAP, k_btonemap, GV, dim3(256), 0, s, (const ViewDev *)dv,
            (const unsigned long long *)r->maxv.p, rp.tone_auto ? 1 : 0);
 }
 
@@ -1358,7 +1444,17 @@ void renderer_release(gblod_renderer *r)
     r->pass_stats.release(A, s);
     r->b_views.release(A, s); r->b_frontA.release(A, s); r->b_frontB.release(A, s); r->b_sel.release(A, s);
     r->b_counts.release(A, s); r->b_pfx.release(A, s); r->b_base.release(A, s);
+    r->d_cams.release(A, s); r->d_rec.release(A, s); r->d_cnt.release(A, s); r->d_off.release(A, s);
+    r->d_cur.release(A, s); r->d_icnt.release(A, s); r->d_ioff.release(A, s); r->d_items.release(A, s);
     r->scan.buf.release(A, s);
+}
+
+void check_format(const gblod_octree *o, const gblod_render_params &rp)
+{
+    if (rp.point_format == GBLOD_POINTS_BLOCK16 ? !o->has_block16 : !o->has_float)
+        fail(GBLOD_ERR_INVALID_ARG, rp.point_format == GBLOD_POINTS_BLOCK16
+                                        ? "octree holds no 16-bit block codes (gblod_octree_quantize)"
+                                        : "octree holds no fp32 points (dropped after quantisation)");
 }
 
 void check_image(const gblod_camera &c)
@@ -1371,6 +1467,7 @@ void render_lod(gblod_renderer *r, const gblod_octree *o, const gblod_camera &ca
                 uint8_t *image, uint64_t *accum, cudaStream_t s)
 {
     check_image(cam);
+    check_format(o, rp);
     r->last_stream = s;
     r->last_was_lod = true;
     const Allocator &A = r->A;
@@ -1386,22 +1483,34 @@ void render_lod(gblod_renderer *r, const gblod_octree *o, const gblod_camera &ca
     r->sel_base.ensure(A, nn + 1, s);
     GB_CUDA(cudaMemsetAsync(r->lvl_cnt.p, 0, (size_t)(levels + 2) * 4, s));
     uint32_t *nsel = r->lvl_cnt.p + levels + 1;
+    const bool q = rp.point_format == GBLOD_POINTS_BLOCK16;
+    const gblod_node *nodes = q ? o->qnodes : o->nodes;
     if (nn > 0) {
         const Frustum fr = make_frustum(cam, rp, o);
         launch(GBLOD_K_SELECT_NODES, k_select_init, dim3(1), dim3(1), 0, s, r->frontA.p, r->lvl_cnt.p);
         uint32_t *fin = r->frontA.p, *fout = r->frontB.p;
         const unsigned G = (unsigned)persistent_blocks(2);
         for (int d = 0; d < levels; ++d) {
-            launch(GBLOD_K_SELECT_NODES, k_select_level, dim3(G), dim3(RT), 0, s, (const gblod_node *)o->nodes, fr,
+            launch(GBLOD_K_SELECT_NODES, k_select_level, dim3(G), dim3(RT), 0, s, nodes, fr,
                    (const uint32_t *)fin, (const uint32_t *)(r->lvl_cnt.p + d), fout, r->lvl_cnt.p + d + 1,
                    r->sel.p, nsel);
             std::swap(fin, fout);
         }
     }
-    launch(GBLOD_K_SELECT_NODES, k_sel_prefix, dim3(1), dim3(1024), 0, s, (const gblod_node *)o->nodes,
-           (const uint32_t *)r->sel.p, (const uint32_t *)nsel, r->sel_pfx.p, r->sel_base.p, r->stats);
+    launch(GBLOD_K_SELECT_NODES, k_sel_prefix, dim3(1), dim3(1024), 0, s, nodes, (const uint32_t *)r->sel.p,
+           (const uint32_t *)nsel, r->sel_pfx.p, r->sel_base.p, r->stats);
     SrcLOD src{o->pts4, o->hs, r->sel_pfx.p, r->sel_base.p, nsel, &r->stats->points};
-    frame_common(r, src, P, rp, image, accum, s);
+    if (q) {
+        SrcLODQ sq;
+        static_cast<SrcLOD &>(sq) = src;
+        sq.q4 = o->q4;
+        sq.qw = o->qw;
+        sq.qa = o->qa;
+        sq.sel = r->sel.p;
+        frame_common(r, sq, P, rp, image, accum, s);
+    } else {
+        frame_common(r, src, P, rp, image, accum, s);
+    }
 }
 
 void render_brute(gblod_renderer *r, const float *xyz, const float *mass, const float *h, uint64_t n,

@@ -31,6 +31,10 @@ struct gblod_renderer {
     gb::DBuf<unsigned long long> b_frontA, b_frontB, b_sel, b_counts, b_pfx;
     gb::DBuf<long long> b_base;
     uint64_t b_rec_cap = 0;
+    // differentiable float splat
+    gb::DBuf<unsigned char> d_cams, d_rec;
+    gb::DBuf<uint32_t> d_cnt, d_off, d_cur, d_icnt, d_ioff;
+    gb::DBuf<uint4> d_items;
     cudaStream_t last_stream = nullptr;
     bool last_was_lod = false;
 };
@@ -49,6 +53,9 @@ gblod_status render_brute_noalloc(const float *xyz, const float *mass, const flo
 void reserve_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod_render_params &rp,
                    uint64_t record_capacity, cudaStream_t s);
 void render_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod_render_params &rp, cudaStream_t s);
+void diff_pass(gblod_renderer *r, const float *xyz, const float *w, const float *logh, uint64_t n,
+               const gblod_camera *cams, int nv, const gblod_render_params &rp, float *images, const float *grad_img,
+               float *gxyz, float *gw, float *glogh, cudaStream_t s);
 void project_points(const float4 *pts4, const float *h, uint64_t n, const gblod_camera &cam,
                     const gblod_render_params &rp, int64_t *out, cudaStream_t s);
 void morton_keys(const float *xyz, uint64_t n, const double lo[3], double side, uint64_t *keys, cudaStream_t s);

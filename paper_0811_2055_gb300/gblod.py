@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "libgblod.so")
 OK, ERR_INVALID_ARG, ERR_RANGE, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_NOT_IMPLEMENTED, ERR_CAPACITY = range(8)
 NODE_LEAF, NODE_INTERNAL, NODE_LOSSY, NODE_REPS = 1, 2, 4, 8
 KERNEL_GAUSSIAN, KERNEL_CUBIC = 0, 1
+POINTS_FLOAT, POINTS_BLOCK16 = 0, 1
+QUANTIZE_DROP_FLOAT = 1
 (K_ANY, K_MORTON, K_SORT_UPSWEEP, K_SORT_SCATTER, K_SCAN, K_BUILD_OTHER, K_SEL_HIST, K_SEL_MARK, K_SEL_WRITE,
  K_SELECT_NODES, K_PROJECT_COUNT, K_PROJECT_SCATTER, K_SPLAT, K_TONEMAP, K_RENDER_OTHER) = range(15)
 
@@ -47,7 +49,7 @@ class RenderParams(C.Structure):
     _fields_ = [("lambda_px", C.c_double), ("sigma_min_px", C.c_double), ("sigma_max_px", C.c_double),
                 ("tone_lo", C.c_double), ("tone_hi", C.c_double), ("kernel", C.c_int32),
                 ("tone_auto", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
-                ("record_budget", C.c_uint64)]
+                ("record_budget", C.c_uint64), ("point_format", C.c_int32), ("reserved", C.c_int32)]
 
 
 class View(C.Structure):
@@ -57,7 +59,7 @@ class View(C.Structure):
 class OctreeInfo(C.Structure):
     _fields_ = [("n_particles", C.c_uint64), ("n_nodes", C.c_uint64), ("n_points", C.c_uint64),
                 ("device_bytes", C.c_uint64), ("depth_max", C.c_int32), ("equal_mass", C.c_int32),
-                ("n_max", C.c_uint32), ("reserved", C.c_uint32)]
+                ("n_max", C.c_uint32), ("formats", C.c_uint32)]
 
 
 class FrameStats(C.Structure):
@@ -84,6 +86,8 @@ _L.gblod_octree_free.argtypes = [_vp]
 _L.gblod_octree_free.restype = None
 _L.gblod_octree_get_info.argtypes = [_vp, C.POINTER(OctreeInfo)]
 _L.gblod_octree_export.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
+_L.gblod_octree_quantize.argtypes = [_vp, _u32, _vp]
+_L.gblod_octree_export_block16.argtypes = [_vp, _vp, _vp, _vp]
 _L.gblod_renderer_create.argtypes = [_vp, C.POINTER(_vp)]
 _L.gblod_renderer_destroy.argtypes = [_vp]
 _L.gblod_renderer_destroy.restype = None
@@ -98,7 +102,13 @@ _L.gblod_renderer_reserve_batch.argtypes = [_vp, C.POINTER(View), _i32, C.POINTE
 _L.gblod_render_batch.argtypes = [_vp, C.POINTER(View), _i32, C.POINTER(RenderParams), _vp]
 _L.gblod_autotune_tiles.argtypes = [_vp, C.POINTER(View), _i32, C.POINTER(RenderParams), _u64, _vp,
                                     C.POINTER(_d)]
+_L.gblod_autotune_cache_clear.argtypes = []
+_L.gblod_autotune_cache_clear.restype = None
 _L.gblod_project.argtypes = [_vp, _vp, _u64, C.POINTER(Camera), C.POINTER(RenderParams), _vp, _vp]
+_L.gblod_diff_render.argtypes = [_vp, _vp, _vp, _vp, _u64, C.POINTER(Camera), _i32, C.POINTER(RenderParams), _vp,
+                                 _vp]
+_L.gblod_diff_backward.argtypes = [_vp, _vp, _vp, _vp, _u64, C.POINTER(Camera), _i32, C.POINTER(RenderParams), _vp,
+                                   _vp, _vp, _vp, _vp]
 _L.gblod_launch_count.restype = _u64
 _L.gblod_probe_enable.argtypes = [_i32]
 _L.gblod_probe_read.argtypes = [C.POINTER(_d), C.POINTER(_u64)]
@@ -108,7 +118,8 @@ _L.gblod_last_error.restype = C.c_char_p
 for _f in ("gblod_build_lod", "gblod_octree_get_info", "gblod_octree_export", "gblod_renderer_create",
            "gblod_render", "gblod_render_bruteforce", "gblod_renderer_status", "gblod_renderer_stats",
            "gblod_renderer_last_selection", "gblod_morton_keys", "gblod_project", "gblod_probe_enable",
-           "gblod_probe_read", "gblod_renderer_reserve_batch", "gblod_render_batch", "gblod_autotune_tiles"):
+           "gblod_probe_read", "gblod_renderer_reserve_batch", "gblod_render_batch", "gblod_autotune_tiles",
+           "gblod_diff_render", "gblod_diff_backward", "gblod_octree_quantize", "gblod_octree_export_block16"):
     getattr(_L, _f).restype = C.c_int
 
 
@@ -143,7 +154,8 @@ def make_camera(cam: dict) -> Camera:
 
 
 def make_params(lambda_px=None, sigma_min_px=0.5, sigma_max_px=128.0, kernel=KERNEL_GAUSSIAN, tone_auto=True,
-                tone_lo=0.0, tone_hi=0.0, tile_w=0, tile_h=0, record_budget=0) -> RenderParams:
+                tone_lo=0.0, tone_hi=0.0, tile_w=0, tile_h=0, record_budget=0,
+                point_format=POINTS_FLOAT) -> RenderParams:
     p = RenderParams()
     p.lambda_px = -1.0 if lambda_px is None else float(lambda_px)
     p.sigma_min_px, p.sigma_max_px = float(sigma_min_px), float(sigma_max_px)
@@ -151,6 +163,7 @@ def make_params(lambda_px=None, sigma_min_px=0.5, sigma_max_px=128.0, kernel=KER
     p.kernel, p.tone_auto = int(kernel), int(bool(tone_auto))
     p.tile_w, p.tile_h = int(tile_w), int(tile_h)
     p.record_budget = int(record_budget)
+    p.point_format = int(point_format)
     return p
 
 
@@ -184,6 +197,22 @@ class Octree:
                                       skey.ctypes.data, sidx.ctypes.data), "gblod_octree_export")
         return dict(nodes=nodes, pts4=pts4, hs=hs, pt_src=src, skey=skey, sidx=sidx, depth_max=int(i.depth_max),
                     equal_mass=bool(i.equal_mass), n_max=int(i.n_max))
+
+    def quantize(self, drop_float: bool = False, stream=None) -> "Octree":
+        """Codes every stored point as 16-bit block codes (gblod_octree_quantize)."""
+        _check(_L.gblod_octree_quantize(self._h, QUANTIZE_DROP_FLOAT if drop_float else 0, _stream(stream)),
+               "gblod_octree_quantize")
+        return self
+
+    def export_block16(self) -> dict:
+        i = self.info()
+        nn, npt = int(i.n_nodes), int(i.n_points)
+        codes = np.zeros((max(npt, 1), 5), np.uint16)
+        qa = np.zeros((max(nn, 1), 8), np.float32)
+        qnodes = np.zeros(max(nn, 1), NODE_DTYPE)
+        _check(_L.gblod_octree_export_block16(self._h, codes.ctypes.data, qa.ctypes.data, qnodes.ctypes.data),
+               "gblod_octree_export_block16")
+        return dict(codes=codes[:npt], qa=qa[:nn], qnodes=qnodes[:nn])
 
     def free(self):
         if self._h:
@@ -285,6 +314,10 @@ class Renderer:
                                        _stream(stream), C.byref(best)), "gblod_autotune_tiles")
         return params, float(best.value)
 
+    @staticmethod
+    def autotune_cache_clear():
+        _L.gblod_autotune_cache_clear()
+
     def status(self, reset: bool = True, stream=None) -> int:
         return int(_L.gblod_renderer_status(self._h, _stream(stream), int(reset)))
 
@@ -312,6 +345,54 @@ class Renderer:
             self.close()
         except Exception:
             pass
+
+
+def _cams(cams):
+    arr = (Camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = make_camera(c)
+    return arr
+
+
+def diff_render(r: Renderer, xyz, w, logh, cams, params: RenderParams | None = None, stream=None) -> torch.Tensor:
+    """Float splat images (n_views, H, W) of points (xyz n x 3, w, logh), see gblod_diff_render."""
+    params = params if params is not None else make_params()
+    n = int(xyz.shape[0])
+    H, W = int(cams[0]["height"]), int(cams[0]["width"])
+    img = torch.empty((len(cams), H, W), dtype=torch.float32, device=xyz.device)
+    _check(_L.gblod_diff_render(r._h, _ptr(xyz), _ptr(w), _ptr(logh), n, _cams(cams), len(cams), C.byref(params),
+                                _ptr(img), _stream(stream)), "gblod_diff_render")
+    return img
+
+
+def diff_backward(r: Renderer, xyz, w, logh, cams, grad_images, params: RenderParams | None = None, stream=None):
+    """dL/dxyz, dL/dw, dL/dlogh from dL/dI (gblod_diff_backward)."""
+    params = params if params is not None else make_params()
+    n = int(xyz.shape[0])
+    gx, gw, gl = torch.empty_like(xyz), torch.empty_like(w), torch.empty_like(logh)
+    grad_images = grad_images.contiguous()
+    _check(_L.gblod_diff_backward(r._h, _ptr(xyz), _ptr(w), _ptr(logh), n, _cams(cams), len(cams), C.byref(params),
+                                  _ptr(grad_images), _ptr(gx), _ptr(gw), _ptr(gl), _stream(stream)),
+           "gblod_diff_backward")
+    return gx, gw, gl
+
+
+class SplatImages(torch.autograd.Function):
+    """images = SplatImages.apply(xyz, w, logh, cams, renderer, params): differentiable float splat
+    whose backward is the library's adjoint kernel (recomputation, nothing stored per pixel)."""
+
+    @staticmethod
+    def forward(ctx, xyz, w, logh, cams, renderer, params):
+        xyz, w, logh = xyz.contiguous(), w.contiguous(), logh.contiguous()
+        ctx.save_for_backward(xyz, w, logh)
+        ctx.cams, ctx.renderer, ctx.params = cams, renderer, params
+        return diff_render(renderer, xyz, w, logh, cams, params)
+
+    @staticmethod
+    def backward(ctx, grad):
+        xyz, w, logh = ctx.saved_tensors
+        gx, gw, gl = diff_backward(ctx.renderer, xyz, w, logh, ctx.cams, grad, ctx.params)
+        return gx, gw, gl, None, None, None
 
 
 def morton_keys(xyz: torch.Tensor, root_lo=(0.0, 0.0, 0.0), root_side: float = 1.0, stream=None) -> torch.Tensor:

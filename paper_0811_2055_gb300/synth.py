@@ -59,6 +59,7 @@ class Particles:
     mass: np.ndarray  # (N,) float32
     h: np.ndarray     # (N,) float32
     name: str = ""
+    vel: np.ndarray | None = None  # (N, 3) float32 drift per timestep (halo bulk motion), optional
 
     @property
     def n(self) -> int:
@@ -124,7 +125,7 @@ def _nfw_radii(rng, n_per_halo, conc, r_vir, n_buckets=64):
 
 def clustered(n: int, n_halos: int, bg_frac: float = 0.10, central_frac: float = 0.0,
               central_c: float = 10.0, central_rvir: float = 0.25, seed: int = SEED_BASE + 1,
-              name: str = "clustered") -> Particles:
+              name: str = "clustered", drift: float = 0.0) -> Particles:
     """NFW-halo recipe: background + power-law halo population (+ optional central halo)."""
     rng = _rng(seed)
     n_bg = int(round(bg_frac * n))
@@ -162,13 +163,26 @@ def clustered(n: int, n_halos: int, bg_frac: float = 0.10, central_frac: float =
     pos = np.concatenate([pos_h, pos_bg], axis=0)
     h = np.concatenate([h_h, h_bg]).astype(np.float32)
     perm = rng.permutation(n)
-    return Particles(_wrap_f32(pos[perm]), np.ones(n, np.float32), h[perm], name)
+    vel = None
+    if drift > 0.0:
+        # halo bulk velocities ~ N(0, drift) per timestep, drawn last so the positions above do not
+        # depend on it; every particle of a halo moves with it, the background stays
+        v_h = rng.normal(0.0, drift, (len(cnt), 3))
+        vel = np.concatenate([v_h[halo], np.zeros((n_bg, 3))], axis=0)[perm].astype(np.float32)
+    return Particles(_wrap_f32(pos[perm]), np.ones(n, np.float32), h[perm], name, vel)
 
 
 def mid(n: int = 1 << 24, seed: int = SEED_BASE + 1) -> Particles:
     """4096 NFW halos + 10% background (16.8M particles at full size)."""
     n_halos = max(1, int(round(4096 * n / (1 << 24))))
     return clustered(n, n_halos, 0.10, 0.0, seed=seed, name=f"mid{n}")
+
+
+def timesteps_recipe(n: int = 75_000_000, seed: int = SEED_BASE + 4) -> Particles:
+    """The serving workload's base snapshot: mid recipe with 32,768 halos at 75M particles, plus
+    halo drift velocities N(0, 0.002) per timestep (timestep t = wrap(xyz + t vel))."""
+    n_halos = max(1, int(round(32768 * n / 75_000_000)))
+    return clustered(n, n_halos, 0.10, 0.0, seed=seed, name=f"timesteps{n}", drift=0.002)
 
 
 def paper_scale(n: int = 150_000_000, seed: int = SEED_BASE + 2) -> Particles:

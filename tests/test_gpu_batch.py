@@ -144,8 +144,16 @@ def test_autotuner_picks_a_tile_and_keeps_the_image(G, scene):
     dev = torch.device("cuda", 0)
     views = _views(dev, [(ta, cams[0]), (tb, cams[4])])
     r = G.Renderer()
+    G.Renderer.autotune_cache_clear()
+    l0 = G.launch_count()
     par, ms = r.autotune(views, G.make_params(), record_capacity=1 << 22)
+    l1 = G.launch_count()
     assert (par.tile_w, par.tile_h) in [(16, 16), (32, 16), (16, 32), (32, 32), (64, 16)] and ms > 0
+    # the same batch again: served from the cache with a single measuring render
+    par2, ms2 = r.autotune(views, G.make_params(), record_capacity=1 << 22)
+    l2 = G.launch_count()
+    assert (par2.tile_w, par2.tile_h) == (par.tile_w, par.tile_h) and ms2 == ms
+    assert (l2 - l1) * 10 < (l1 - l0)
     r.render_batch(views, par)
     torch.cuda.synchronize()
     alone = G.Renderer()
