@@ -39,7 +39,8 @@ def args_():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-block16", action="store_true", help="skip the 16-bit block-code fly-through")
-    ap.add_argument("--workload", choices=["mid", "paper", "tiny", "diff", "serve"], default="mid")
+    ap.add_argument("--workload", choices=["mid", "paper", "tiny", "diff", "serve", "paper-views"], default="mid")
+    ap.add_argument("--repeats", type=int, default=20, help="paper-views: timed repeats per view")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of offered load")
     ap.add_argument("--sessions", type=int, default=64)
     ap.add_argument("--session-budget-gb", type=float, default=4.0)
@@ -584,6 +585,93 @@ def run_diff(a):
     print(json.dumps(line), flush=True)
 
 
+def run_paper_views(a):
+    """Paper-scale timestep (150M particles): build, then every one of the eight views at 1920x1080
+    and 3840x2160, LOD and all points, each timed `--repeats` times (p50/p99 per view)."""
+    import torch
+
+    from paper_0811_2055_gb300 import gblod, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    p = synth.paper_scale(a.particles) if a.particles else synth.paper_scale()
+    t_gen = time.perf_counter() - t0
+    xyz, mass, h = (torch.from_numpy(x).to(dev) for x in (p.xyz, p.mass, p.h))
+    n_max = 16000
+    lam = math.sqrt(n_max)
+    r = gblod.Renderer()
+    par = gblod.make_params(lambda_px=lam)
+    bms = []
+    for _ in range(3 + a.warmup):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tree = gblod.build_lod(xyz, mass, h, n_max=n_max, seed=1)
+        e1.record()
+        torch.cuda.synchronize()
+        bms.append(e0.elapsed_time(e1))
+        info = tree.info()
+        tree.free()
+    bms = bms[a.warmup:]
+    tree = gblod.build_lod(xyz, mass, h, n_max=n_max, seed=1)
+    info = tree.info()
+    peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    def timed(fn, reps):
+        for _ in range(a.warmup):
+            fn()
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    views = []
+    lod_1080 = []
+    clocks = Clocks(0)
+    for (W, H) in ((1920, 1080), (3840, 2160)):
+        img = torch.empty((H, W), dtype=torch.uint8, device=dev)
+        acc = torch.empty((H, W), dtype=torch.int64, device=dev)
+        for j in range(8):
+            cam = synth.paper_view(j, W, H)
+            lms = timed(lambda: r.render(tree, cam, par, image=img, accum=acc), a.repeats)
+            ls = r.stats()
+            bms_ = timed(lambda: r.render_bruteforce(xyz, mass, h, cam, par, image=img, accum=acc), a.repeats)
+            bs = r.stats()
+            b_bytes = 20 * p.n + W * H
+            v = {"view": j, "resolution": f"{W}x{H}", "lod_p50_ms": float(np.percentile(lms, 50)),
+                 "lod_p99_ms": float(np.percentile(lms, 99)), "lod_fps": 1e3 / float(np.mean(lms)),
+                 "lod_splats": ls["splats"], "lod_points": ls["points"], "lod_pixel_updates": ls["pixel_updates"],
+                 "lod_splats_per_s": ls["splats"] / (float(np.mean(lms)) / 1e3),
+                 "all_p50_ms": float(np.percentile(bms_, 50)), "all_p99_ms": float(np.percentile(bms_, 99)),
+                 "all_fps": 1e3 / float(np.mean(bms_)), "all_splats": bs["splats"],
+                 "all_pixel_updates": bs["pixel_updates"],
+                 "all_hbm_frac": b_bytes / (float(np.mean(bms_)) / 1e3) / (hbm * 1e9)}
+            views.append(v)
+            if H == 1080:
+                lod_1080.append(float(np.mean(lms)))
+    ck = clocks.stop()
+    assert r.status() == gblod.OK
+    line = {"metric": "1080p LOD frames/s over the eight paper-scale views (150M particles); per-view LOD and "
+                      "all-points frames/s, splats/s, p50/p99",
+            "value": 8 / (sum(lod_1080) / 1e3), "unit": "frames/s", "n_gpus": 1, "steps": a.repeats,
+            "warmup": a.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 projection, u64 fixed-point accumulation, f64 node criterion", "data": "synthetic",
+            "config": {"workload": "paper: 150M particles (65,536 NFW halos + central halo with 30% + 10% uniform), "
+                                   "n_max 16000, eight views d_j = 0.01 * 150^(j/7) from the central halo, "
+                                   "1920x1080 and 3840x2160", "particles": p.n, "octree_nodes": int(info.n_nodes),
+                       "octree_points": int(info.n_points), "octree_bytes": int(info.device_bytes)},
+            "build_ms": float(np.median(bms)), "build_particles_per_s": p.n / (float(np.median(bms)) / 1e3),
+            "generate_s": t_gen, "hbm_gbs_peak": hbm, "views": views, "clocks": ck}
+    tree.free()
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(a):
     """Serving workload: 16 device-resident timesteps (halo drift), 64 viewer sessions at mixed
     resolutions (720p/1080p/4K) with Poisson requests at 30 Hz each, admission by an HBM budget,
@@ -643,6 +731,8 @@ def main():
         run_diff(a)
     elif a.workload == "serve":
         run_serve(a)
+    elif a.workload == "paper-views":
+        run_paper_views(a)
     else:
         run_ours(a)
 

@@ -191,8 +191,8 @@ typedef struct {
     double tone_lo, tone_hi; /* fixed log range in intensity units (used when tone_auto == 0) */
     int32_t kernel;       /* GBLOD_KERNEL_* */
     int32_t tone_auto;    /* 1: hi = image maximum, lo = 1e-4 hi */
-    int32_t tile_w, tile_h; /* screen tile, 1..64 each, covering at most 32 blocks of 8 x 4
-                             pixels (ceil(w/8) ceil(h/4) <= 32; 0 = 32); any value gives the
+    int32_t tile_w, tile_h; /* screen tile, 1..64 each, covering at most 8 strips of 8 x 16
+                             pixels (ceil(w/8) ceil(h/16) <= 8; 0 = 32); any value gives the
                              same image */
     uint64_t record_budget; /* most (tile, splat) records held at once (16 bytes each); 0 = 2^28,
                              capped at 2^31.  A frame needing more is binned and splatted in

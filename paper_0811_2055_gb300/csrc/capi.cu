@@ -56,8 +56,8 @@ gblod_render_params check_params(const gblod_render_params *p)
     if (q.tile_w == 0) q.tile_w = 32;
     if (q.tile_h == 0) q.tile_h = 32;
     if (q.tile_w < 1 || q.tile_h < 1 || q.tile_w > 64 || q.tile_h > 64 ||
-        ((q.tile_w + 7) / 8) * ((q.tile_h + 3) / 4) > 32)
-        fail(GBLOD_ERR_INVALID_ARG, "tile must be 1..64 x 1..64 and cover at most 32 blocks of 8 x 4 pixels");
+        ((q.tile_w + 7) / 8) * ((q.tile_h + 15) / 16) > 8)
+        fail(GBLOD_ERR_INVALID_ARG, "tile must be 1..64 x 1..64 with ceil(w/8) ceil(h/16) <= 8 (8 strips of 8 x 16 pixels)");
     if (!q.tone_auto && !(q.tone_hi > q.tone_lo && q.tone_lo > 0.0 && std::isfinite(q.tone_hi)))
         fail(GBLOD_ERR_INVALID_ARG, "fixed tone range needs 0 < tone_lo < tone_hi < inf");
     if (q.point_format != GBLOD_POINTS_FLOAT && q.point_format != GBLOD_POINTS_BLOCK16)

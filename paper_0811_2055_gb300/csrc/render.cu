@@ -561,10 +561,10 @@ static_assert(ITEM <= (1u << 15), "32-bit partial sums need at most 2^15 records
 
 struct SplatSmem {
     int32_t K[1024];
-    int4 A[RT];                             // U, V, S, Wh = Wq >> 16
-    uint4 B[RT];                            // QL low, QL high, Wl = Wq & 0xFFFF, unused
-    uint8_t list[RT / 32][SPLAT_SLOTS][RT]; // per warp and block: small records from the front,
-                                            // large ones from the back
+    int4 A[RT];                // U, V, S, Wh = Wq >> 16
+    uint4 B[RT];               // QL low, Wl = Wq & 0xFFFF, QL high, unused
+    uint16_t list[RT / 32][RT]; // per warp: record | touched blocks of its strip << 8; small records
+                                // from the front, large ones from the back
 };
 
 // A record is "small" when QL <= 2^30: every pixel of a block its support reaches then lies
@@ -572,7 +572,20 @@ struct SplatSmem {
 // table index (q S) >> 37 is the high word of a 32 x 32 product shifted by 5.
 constexpr unsigned long long QL_SMALL = 1ull << 30;
 
-// Splats records [it.y, it.z) of tile `tile` (index inside the view) of view P into img.
+// Each warp owns up to SPLAT_SLOTS blocks of 8 x 4 pixels in one block column: with the tile's
+// nbx x nby blocks, sh = the smallest count with nbx ceil(nby / sh) <= 8 warps, warp w takes column
+// w % nbx and the block rows g, g + ng, g + 2 ng, ... (g = w / nbx, ng = ceil(nby / sh)), so the
+// rows of a column are interleaved between its warps and their work stays balanced.
+__host__ __device__ __forceinline__ int strip_height(int nbx, int nby)
+{
+    int sh = 1;
+    while (sh < SPLAT_SLOTS && nbx * ((nby + sh - 1) / sh) > RT / 32) ++sh;
+    return sh;
+}
+
+// Splats records [it.y, it.z) of tile `tile` (index inside the view) of view P into img.  Each
+// lane owns one pixel column position of its warp's strip and one pixel in every block of it;
+// a record's centre offset in x and its square are computed once per strip, not once per block.
 __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const uint4 it, const uint32_t tile,
                                            const Proj &P, unsigned long long *__restrict__ img, SplatSmem &sm,
                                            unsigned &hits)
@@ -582,14 +595,32 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
     const int tx = (int)(tile % (uint32_t)P.tiles_x), ty = (int)(tile / (uint32_t)P.tiles_x);
     const int X0 = tx * P.TW, Y0 = ty * P.TH;
     const int TWc = min(P.TW, P.W - X0), THc = min(P.TH, P.H - Y0); // tile clipped to the image
-    const int nbx = (P.TW + 7) >> 3, nblk = nbx * ((P.TH + 3) >> 2);
+    const int nbx = (P.TW + 7) >> 3, nby = (P.TH + 3) >> 2;
+    const int sh = strip_height(nbx, nby);
+    const int ng = (nby + sh - 1) / sh;                    // row groups
+    const int scol = warp % nbx, srow = warp / nbx;         // block column, first block row
+    const bool active = warp < nbx * ng;                    // warp-uniform
+    const int bx0 = scol * 8;
+    const int pxl = bx0 + (lane & 7), pyl0 = srow * 4 + (lane >> 3);
+    const int pxv = (X0 + pxl) * 256 + 128, pyv0 = (Y0 + pyl0) * 256 + 128;
+    // blocks k of the strip that exist inside the clipped tile; their pixel-centre rectangles
+    unsigned kvalid = 0;
+#pragma unroll
+    for (int k = 0; k < SPLAT_SLOTS; ++k)
+        if (k < sh && srow + k * ng < nby && bx0 < TWc && (srow + k * ng) * 4 < THc) kvalid |= 1u << k;
+    if (!active) kvalid = 0;
+    const int cx0 = (X0 + bx0) * 256 + 128, cx1 = (X0 + min(bx0 + 7, TWc - 1)) * 256 + 128;
     unsigned long long acc[SPLAT_SLOTS];
     uint32_t acc_lo[SPLAT_SLOTS];
+    unsigned hk[SPLAT_SLOTS];
 #pragma unroll
     for (int k = 0; k < SPLAT_SLOTS; ++k) {
         acc[k] = 0ull;
         acc_lo[k] = 0u;
+        hk[k] = 0u;
     }
+    const int dstep = ng * 1024; // y offset between the warp's consecutive blocks, 1/256 px
+    uint16_t *lst = sm.list[warp];
     for (uint32_t base = it.y; base < it.z; base += RT) {
         __syncthreads();
         const int nb = (int)min((uint32_t)RT, it.z - base);
@@ -598,91 +629,97 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
             const unsigned long long Wq = __float2ull_rn(__uint_as_float(R.w));
             const unsigned long long QL = 140737488355327ull / (unsigned long long)R.z + 1ull;
             sm.A[threadIdx.x] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)(Wq >> 16));
-            sm.B[threadIdx.x] = make_uint4((uint32_t)QL, (uint32_t)(QL >> 32), (uint32_t)(Wq & 0xFFFFull), 0u);
+            sm.B[threadIdx.x] = make_uint4((uint32_t)QL, (uint32_t)(Wq & 0xFFFFull), (uint32_t)(QL >> 32), 0u);
         }
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < SPLAT_SLOTS; ++k) {
-            const int b = warp + k * (RT / 32);
-            if (b >= nblk) break; // warp-uniform
-            const int bx0 = (b % nbx) * 8, by0 = (b / nbx) * 4;
-            if (bx0 >= TWc || by0 >= THc) continue;
-            // records whose support reaches a pixel centre of this block (exact test q_min < QL
-            // against the nearest point of the block's pixel-centre rectangle)
-            const int cx0 = (X0 + bx0) * 256 + 128, cx1 = (X0 + min(bx0 + 7, TWc - 1)) * 256 + 128;
-            const int cy0 = (Y0 + by0) * 256 + 128, cy1 = (Y0 + min(by0 + 3, THc - 1)) * 256 + 128;
-            uint8_t *lst = sm.list[warp][k];
-            int ns = 0, nl = 0;
-            for (int j0 = 0; j0 < nb; j0 += 32) {
-                const int j = j0 + lane;
-                bool ts = false, tl = false;
-                if (j < nb) {
-                    const int4 A = sm.A[j];
-                    const uint4 B = sm.B[j];
-                    const long long ex = (long long)A.x - (long long)min(max(A.x, cx0), cx1);
-                    const long long ey = (long long)A.y - (long long)min(max(A.y, cy0), cy1);
-                    const unsigned long long qm = (unsigned long long)(ex * ex + ey * ey);
-                    const unsigned long long QL = ((unsigned long long)B.y << 32) | B.x;
-                    const bool touch = qm < QL;
-                    const bool small = QL <= QL_SMALL;
-                    ts = touch && small;
-                    tl = touch && !small;
-                }
-                const uint32_t ms = __ballot_sync(0xffffffffu, ts), ml = __ballot_sync(0xffffffffu, tl);
-                if (ts) lst[ns + __popc(ms & lt)] = (uint8_t)j;
-                if (tl) lst[RT - 1 - (nl + __popc(ml & lt))] = (uint8_t)j;
-                ns += __popc(ms);
-                nl += __popc(ml);
-            }
-            __syncwarp();
-            const int pxl = bx0 + (lane & 7), pyl = by0 + (lane >> 3);
-            const int pxv = (X0 + pxl) * 256 + 128, pyv = (Y0 + pyl) * 256 + 128;
-            unsigned long long a = acc[k];
-            uint32_t al = acc_lo[k];
-            unsigned hk = 0;
-            // lanes whose pixel lies outside the tile compute too; their sums are never stored
-#pragma unroll 4
-            for (int i = 0; i < ns; ++i) {
-                const int j = lst[i];
+        if (!kvalid) continue; // warp-uniform
+        // records whose support reaches a pixel centre of a block of this strip: exact test
+        // q_min < QL against each block's pixel-centre rectangle
+        int ns = 0, nl = 0;
+        for (int j0 = 0; j0 < nb; j0 += 32) {
+            const int j = j0 + lane;
+            unsigned m = 0;
+            bool small = false;
+            if (j < nb) {
                 const int4 A = sm.A[j];
-                const uint2 B = make_uint2(sm.B[j].x, sm.B[j].z);
-                const int dx = pxv - A.x, dy = pyv - A.y;
-                const uint32_t q = (uint32_t)(dx * dx) + (uint32_t)(dy * dy);
+                const uint4 B = sm.B[j];
+                const unsigned long long QL = ((unsigned long long)B.z << 32) | B.x;
+                small = QL <= QL_SMALL;
+                const long long ex = (long long)A.x - (long long)min(max(A.x, cx0), cx1);
+                const unsigned long long ex2 = (unsigned long long)(ex * ex);
+#pragma unroll
+                for (int k = 0; k < SPLAT_SLOTS; ++k) {
+                    if (!(kvalid >> k & 1u)) continue;
+                    const int by = (srow + k * ng) * 4;
+                    const int cy0 = (Y0 + by) * 256 + 128, cy1 = (Y0 + min(by + 3, THc - 1)) * 256 + 128;
+                    const long long ey = (long long)A.y - (long long)min(max(A.y, cy0), cy1);
+                    if (ex2 + (unsigned long long)(ey * ey) < QL) m |= 1u << k;
+                }
+            }
+            const bool ts = m && small, tl = m && !small;
+            const uint32_t ms = __ballot_sync(0xffffffffu, ts), ml = __ballot_sync(0xffffffffu, tl);
+            const uint16_t e = (uint16_t)(j | (m << 8));
+            if (ts) lst[ns + __popc(ms & lt)] = e;
+            if (tl) lst[RT - 1 - (nl + __popc(ml & lt))] = e;
+            ns += __popc(ms);
+            nl += __popc(ml);
+        }
+        __syncwarp();
+        // lanes whose pixel lies outside the tile compute too; their sums are never stored
+#pragma unroll 2
+        for (int i = 0; i < ns; ++i) {
+            const uint32_t e = lst[i];
+            const int j = e & 255;
+            const int4 A = sm.A[j];
+            const uint2 B = *reinterpret_cast<const uint2 *>(&sm.B[j]); // QL, Wl
+            const int dx = pxv - A.x;
+            const uint32_t dx2 = (uint32_t)(dx * dx);
+            const int dy0 = pyv0 - A.y;
+#pragma unroll
+            for (int k = 0; k < SPLAT_SLOTS; ++k) {
+                if (!(e >> (8 + k) & 1u)) continue; // warp-uniform
+                const int dy = dy0 + k * dstep;
+                const uint32_t q = dx2 + (uint32_t)(dy * dy);
                 if (q < B.x) {
                     const uint32_t idx = __umulhi(q, (uint32_t)A.z) >> 5;
                     const uint32_t kv = (uint32_t)sm.K[idx];
-                    a += (unsigned long long)(uint32_t)A.w * kv;
-                    al += (B.y * kv) >> 16;
-                    ++hk;
+                    acc[k] += (unsigned long long)(uint32_t)A.w * kv;
+                    acc_lo[k] += (B.y * kv) >> 16;
+                    ++hk[k];
                 }
             }
-            for (int i = RT - nl; i < RT; ++i) {
-                const int j = lst[i];
-                const int4 A = sm.A[j];
-                const uint4 B = sm.B[j];
-                const int dx = pxv - A.x, dy = pyv - A.y;
-                const unsigned long long q = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
-                const unsigned long long QL = ((unsigned long long)B.y << 32) | B.x;
+        }
+        for (int i = RT - nl; i < RT; ++i) {
+            const uint32_t e = lst[i];
+            const int j = e & 255;
+            const int4 A = sm.A[j];
+            const uint4 B = sm.B[j];
+            const unsigned long long QL = ((unsigned long long)B.z << 32) | B.x;
+            const int dx = pxv - A.x;
+            const long long dx2 = (long long)dx * dx;
+            const int dy0 = pyv0 - A.y;
+#pragma unroll
+            for (int k = 0; k < SPLAT_SLOTS; ++k) {
+                if (!(e >> (8 + k) & 1u)) continue;
+                const int dy = dy0 + k * dstep;
+                const unsigned long long q = (unsigned long long)(dx2 + (long long)dy * dy);
                 if (q < QL) {
                     const uint32_t idx = (uint32_t)((q * (unsigned long long)(uint32_t)A.z) >> 37);
                     const uint32_t kv = (uint32_t)sm.K[idx];
-                    a += (unsigned long long)(uint32_t)A.w * kv;
-                    al += (B.z * kv) >> 16;
-                    ++hk;
+                    acc[k] += (unsigned long long)(uint32_t)A.w * kv;
+                    acc_lo[k] += (B.y * kv) >> 16;
+                    ++hk[k];
                 }
             }
-            if (pxl < TWc && pyl < THc) hits += hk;
-            acc[k] = a;
-            acc_lo[k] = al;
         }
     }
 #pragma unroll
     for (int k = 0; k < SPLAT_SLOTS; ++k) {
-        const int b = warp + k * (RT / 32);
-        if (b >= nblk) break;
-        const int pxl = (b % nbx) * 8 + (lane & 7), pyl = (b / nbx) * 4 + (lane >> 3);
+        const int pyl = pyl0 + 4 * ng * k;
+        if (!(kvalid >> k & 1u) || pxl >= TWc || pyl >= THc) continue;
+        hits += hk[k];
         const unsigned long long v = acc[k] + acc_lo[k];
-        if (pxl < TWc && pyl < THc && v) atomicAdd(&img[(size_t)(Y0 + pyl) * P.W + (X0 + pxl)], v);
+        if (v) atomicAdd(&img[(size_t)(Y0 + pyl) * P.W + (X0 + pxl)], v);
     }
 }
 

@@ -101,7 +101,8 @@ def test_full_depth_lod_equals_bruteforce(G, R):
         assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("tile", [(8, 8), (32, 8), (32, 16), (1, 1), (32, 32), (64, 16), (13, 7)])
+@pytest.mark.parametrize("tile", [(8, 8), (32, 8), (32, 16), (1, 1), (32, 32), (64, 16), (13, 7), (24, 32), (8, 64),
+                                  (64, 8), (5, 50)])
 def test_tiling_does_not_change_the_image(G, R, tile):
     p = synth.tiny(30000, seed=24)
     cam = _cams()["inside"]
@@ -189,6 +190,8 @@ def test_invalid_arguments(G, R):
         R.render_bruteforce(*to_dev(p.xyz, p.mass, p.h), _cams()["outside"], G.make_params(tile_w=64, tile_h=64))
     with pytest.raises(G.GblodError):
         R.render_bruteforce(*to_dev(p.xyz, p.mass, p.h), _cams()["outside"], G.make_params(tile_w=17, tile_h=60))
+    with pytest.raises(G.GblodError):  # 5 columns of strips x 2 rows: more than 8 warps
+        R.render_bruteforce(*to_dev(p.xyz, p.mass, p.h), _cams()["outside"], G.make_params(tile_w=40, tile_h=24))
     with pytest.raises(G.GblodError):
         R.render_bruteforce(*to_dev(p.xyz, p.mass, p.h), _cams()["outside"], G.make_params(sigma_min_px=0.0))
 
