@@ -561,11 +561,20 @@ static_assert(ITEM <= (1u << 15), "32-bit partial sums need at most 2^15 records
 
 struct SplatSmem {
     int32_t K[1024];
+    uint4 raw[RT];             // records of the next stage, copied asynchronously
     int4 A[RT];                // U, V, S, Wh = Wq >> 16
     uint4 B[RT];               // QL low, Wl = Wq & 0xFFFF, QL high, unused
     uint16_t list[RT / 32][RT]; // per warp: record | touched blocks of its strip << 8; small records
                                 // from the front, large ones from the back
 };
+
+// 16-byte global -> shared copy that bypasses registers and L1 (completes at cp_async_wait_all)
+__device__ __forceinline__ void cp_async16(uint32_t smem_addr, const uint4 *g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // A record is "small" when QL <= 2^30: every pixel of a block its support reaches then lies
 // within 2^15 + 8 px of its centre on each axis (in 1/256 px), so dx^2 + dy^2 < 2^32 and the
@@ -621,17 +630,24 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
     }
     const int dstep = ng * 1024; // y offset between the warp's consecutive blocks, 1/256 px
     uint16_t *lst = sm.list[warp];
+    // records reach shared memory through `raw`, copied (cp.async) one stage ahead of their use
+    const uint32_t raw_addr = (uint32_t)__cvta_generic_to_shared(&sm.raw[threadIdx.x]);
+    if (it.y + threadIdx.x < it.z) cp_async16(raw_addr, rec + it.y + threadIdx.x);
+    cp_async_commit();
     for (uint32_t base = it.y; base < it.z; base += RT) {
+        cp_async_wait_all();
         __syncthreads();
         const int nb = (int)min((uint32_t)RT, it.z - base);
         if ((int)threadIdx.x < nb) {
-            const uint4 R = rec[base + threadIdx.x];
+            const uint4 R = sm.raw[threadIdx.x];
             const unsigned long long Wq = __float2ull_rn(__uint_as_float(R.w));
             const unsigned long long QL = 140737488355327ull / (unsigned long long)R.z + 1ull;
             sm.A[threadIdx.x] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)(Wq >> 16));
             sm.B[threadIdx.x] = make_uint4((uint32_t)QL, (uint32_t)(Wq & 0xFFFFull), (uint32_t)(QL >> 32), 0u);
         }
         __syncthreads();
+        if (base + RT + threadIdx.x < it.z) cp_async16(raw_addr, rec + base + RT + threadIdx.x);
+        cp_async_commit();
         if (!kvalid) continue; // warp-uniform
         // records whose support reaches a pixel centre of a block of this strip: exact test
         // q_min < QL against each block's pixel-centre rectangle
