@@ -428,6 +428,30 @@ __device__ __forceinline__ void src_load(const SrcFlat &s, unsigned long long e,
     h = s.h[e];
 }
 
+// Sum of drawn amplitudes as 128 bits per thread; one atomic pair per warp at the end (the sum
+// must stay below 2^64, reading R-19)
+struct AmpSum {
+    unsigned long long lo = 0, hi = 0;
+    __device__ __forceinline__ void add(unsigned long long v)
+    {
+        lo += v;
+        hi += lo < v ? 1ull : 0ull;
+    }
+    __device__ __forceinline__ void flush(FrameStatsDev *stats)
+    {
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long ol = __shfl_xor_sync(0xffffffffu, lo, d), oh = __shfl_xor_sync(0xffffffffu, hi, d);
+            lo += ol;
+            hi += oh + (lo < ol ? 1ull : 0ull);
+        }
+        if ((threadIdx.x & 31) == 0 && (lo | hi)) {
+            const unsigned long long old = lo ? atomicAdd(&stats->amp_lo, lo) : 0ull;
+            const unsigned long long carry = lo && old + lo < old ? 1ull : 0ull;
+            if (hi + carry) atomicAdd(&stats->amp_hi, hi + carry);
+        }
+    }
+};
+
 template <class Src>
 __global__ void __launch_bounds__(RT) k_project_count(Src src, Proj P, unsigned long long e_lo,
                                                       unsigned long long e_hi, uint32_t *__restrict__ tile_cnt,
@@ -436,6 +460,7 @@ __global__ void __launch_bounds__(RT) k_project_count(Src src, Proj P, unsigned 
     const unsigned long long total = min(src_total(src), e_hi);
     const int lane = threadIdx.x & 31;
     unsigned long long splats = 0, pairs = 0;
+    AmpSum amp;
     for (unsigned long long a = e_lo + (unsigned long long)blockIdx.x * CHUNK; a < total;
          a += (unsigned long long)gridDim.x * CHUNK) {
         const unsigned long long b = min(total, a + CHUNK);
@@ -451,13 +476,8 @@ __global__ void __launch_bounds__(RT) k_project_count(Src src, Proj P, unsigned 
                 res = project(P, x, y, z, w, h, s);
             }
             if (__any_sync(0xffffffffu, res < 0) && lane == 0) atomicOr(status, ST_RANGE);
-            unsigned long long wq = res == 1 ? __float2ull_rn(s.Wf) : 0ull;
-            for (int d = 16; d > 0; d >>= 1) wq += __shfl_xor_sync(0xffffffffu, wq, d);
-            if (lane == 0 && wq) {
-                const unsigned long long old = atomicAdd(&stats->amp_lo, wq);
-                if (old + wq < old) atomicAdd(&stats->amp_hi, 1ull);
-            }
             if (res == 1) {
+                amp.add(__float2ull_rn(s.Wf));
                 ++splats;
                 int x0, x1, y0, y1;
                 splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
@@ -482,6 +502,7 @@ __global__ void __launch_bounds__(RT) k_project_count(Src src, Proj P, unsigned 
     }
     if (lane == 0 && splats) atomicAdd(&stats->splats, splats);
     if (lane == 0 && pairs) atomicAdd(&stats->pairs, pairs);
+    amp.flush(stats);
 }
 
 template <class Src>
@@ -1134,6 +1155,7 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
     const int lane = threadIdx.x & 31;
     const uint32_t lt = gbd::lanemask_lt();
     unsigned long long splats = 0, pairs = 0;
+    AmpSum amp;
     __shared__ Proj sP[2];
     __shared__ int sV[2];
     for (unsigned long long a = (unsigned long long)blockIdx.x * CHUNK; a < total;
@@ -1160,12 +1182,7 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
             }
             if (!SCATTER) {
                 if (__any_sync(0xffffffffu, res < 0) && lane == 0) atomicOr(status, ST_RANGE);
-                unsigned long long wq = res == 1 ? __float2ull_rn(s.Wf) : 0ull;
-                for (int d = 16; d > 0; d >>= 1) wq += __shfl_xor_sync(0xffffffffu, wq, d);
-                if (lane == 0 && wq) {
-                    const unsigned long long old = atomicAdd(&stats->amp_lo, wq);
-                    if (old + wq < old) atomicAdd(&stats->amp_hi, 1ull);
-                }
+                if (res == 1) amp.add(__float2ull_rn(s.Wf));
             }
             if (res == 1) {
                 const Proj &P = v == sV[0] ? sP[0] : (v == sV[1] ? sP[1] : src.views[v].P);
@@ -1205,6 +1222,7 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
         }
         if (lane == 0 && splats) atomicAdd(&stats->splats, splats);
         if (lane == 0 && pairs) atomicAdd(&stats->pairs, pairs);
+        amp.flush(stats);
     }
 }
 
