@@ -163,6 +163,8 @@ def run_ours(a):
     r = gblod.Renderer()
     lam = math.sqrt(n_max)
     par = gblod.make_params(lambda_px=lam)
+    # the untimed census frames also count their pixel updates (same frames as the timed ones)
+    par_count = gblod.make_params(lambda_px=lam, count_updates=True)
     img = torch.empty((H, W), dtype=torch.uint8, device=dev)
     acc = torch.empty((H, W), dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -202,7 +204,6 @@ def run_ours(a):
         torch.cuda.synchronize()
         tot_ms, frame_ms, build_ms = 0.0, [], []
         l0 = gblod.launch_count()
-        upd0 = r.stats()["pixel_updates_total"]
         if probe is not None:
             gblod.probe_enable(probe)
         for _ in range(steps):
@@ -227,15 +228,17 @@ def run_ours(a):
         pr = gblod.probe_read() if probe is not None else None
         if probe is not None:
             gblod.probe_enable(gblod.K_ANY)
-        upd = r.stats()["pixel_updates_total"] - upd0
-        return tot_ms, frame_ms, build_ms, launches, pr, upd
+        return tot_ms, frame_ms, build_ms, launches, pr
 
     # census of one LOD pass and one brute pass (untimed; the counts are deterministic)
     tree = lod_step()
-    lod_counts = {"splats": 0, "points": 0, "pixel_updates": 0, "nodes": 0}
-    for cam in cams:
-        r.render(tree, cam, par, image=img, accum=acc)
+    lod_counts = {"splats": 0, "points": 0, "pixel_updates": 0, "nodes": 0, "pairs": 0, "pairs_first": 0}
+    for k, cam in enumerate(cams):
+        r.render(tree, cam, par_count, image=img, accum=acc)
         s = r.stats()
+        lod_counts["pairs"] += s["pairs"]
+        if k == 0:
+            lod_counts["pairs_first"] = s["pairs"]
         lod_counts["splats"] += s["splats"]
         lod_counts["points"] += s["points"]
         lod_counts["pixel_updates"] += s["pixel_updates"]
@@ -256,8 +259,8 @@ def run_ours(a):
     assert r.status() == gblod.OK
 
     clocks = Clocks(local)
-    tot_ms, frame_ms, build_ms, launches, pr, upd = timed(lod_step, 2 + 2 * nf, a.steps, a.warmup,
-                                                          probe=gblod.K_SPLAT)
+    tot_ms, frame_ms, build_ms, launches, pr = timed(lod_step, 2 + 2 * nf, a.steps, a.warmup, probe=gblod.K_SPLAT)
+    upd = a.steps * lod_counts["pixel_updates"]  # pixel updates of the timed splat launches (census counts)
     ck = clocks.stop()
 
     # 16-bit block codes (storage paragraph): the same fly-through drawn from 10-byte points
@@ -310,11 +313,11 @@ def run_ours(a):
     if not a.no_brute:
         b_counts = {"splats": 0, "pixel_updates": 0}
         for cam in cams:
-            r.render_bruteforce(xyz, mass, h, cam, par, image=img, accum=acc)
+            r.render_bruteforce(xyz, mass, h, cam, par_count, image=img, accum=acc)
             s = r.stats()
             b_counts["splats"] += s["splats"]
             b_counts["pixel_updates"] += s["pixel_updates"]
-        b_ms, b_frames, _, _, _, _ = timed(brute_step, 2 * nf, a.steps, a.warmup)
+        b_ms, b_frames, _, _, _ = timed(brute_step, 2 * nf, a.steps, a.warmup)
         brute = dict(frames_per_s=a.steps * nf / (b_ms / 1e3), ms_per_frame=b_ms / (a.steps * nf),
                      splats_per_s=a.steps * b_counts["splats"] / (b_ms / 1e3),
                      points_per_s=a.steps * nf * p.n / (b_ms / 1e3),
@@ -448,7 +451,11 @@ def run_ours(a):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": {"kernel": "k_splat_tiles (R3)", "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak if peak else None, "traffic": None,
+                     "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak if peak else None,
+                     "traffic": splat_traffic(a, lod_counts, nf),
+                     "traffic_note": "DRAM read + write bytes of one ncu capture of the splat kernel (first frame of the "
+                                     "mid fly-through), scaled to the mean launch by its (tile, splat) records; null "
+                                     "when the kernel source differs from the captured one or the workload is not mid",
                      "launches": int(splat_launches), "avg_launch_ms": splat_ms / max(splat_launches, 1),
                      "peak_note": "152 SMs x 128 lanes x 2070 MHz (no measured ALU peak in MEASURED_PEAKS.json)"},
     }
@@ -457,6 +464,27 @@ def run_ours(a):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def splat_traffic(a, lod_counts, nf):
+    """DRAM bytes per splat launch from the committed ncu summary, if it was taken of this kernel source."""
+    import hashlib
+    import re
+    root = os.path.dirname(os.path.abspath(__file__))
+    try:
+        prof = open(os.path.join(root, "profiles", "k_splat_tiles_mid_1080p.md")).read()
+        src = open(os.path.join(root, "paper_0811_2055_gb300", "csrc", "render.cu"), "rb").read()
+    except OSError:
+        return None
+    m = re.search(r"render\.cu sha256: ([0-9a-f]{64})", prof)
+    rd = re.search(r"`dram__bytes_read\.sum` \| ([0-9.]+) Mbyte", prof)
+    wr = re.search(r"`dram__bytes_write\.sum` \| ([0-9.]+) Mbyte", prof)
+    if not (m and rd and wr) or m.group(1) != hashlib.sha256(src).hexdigest():
+        return None
+    if a.workload != "mid" or a.particles or not lod_counts["pairs_first"]:
+        return None
+    captured = (float(rd.group(1)) + float(wr.group(1))) * 1e6
+    return captured * (lod_counts["pairs"] / nf) / lod_counts["pairs_first"]
 
 
 # ------------------------------------------------------------------ the oracle (CPU)
@@ -601,6 +629,7 @@ def run_paper_views(a):
     lam = math.sqrt(n_max)
     r = gblod.Renderer()
     par = gblod.make_params(lambda_px=lam)
+    par_count = gblod.make_params(lambda_px=lam, count_updates=True)
     bms = []
     for _ in range(3 + a.warmup):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -640,8 +669,10 @@ def run_paper_views(a):
         for j in range(8):
             cam = synth.paper_view(j, W, H)
             lms = timed(lambda: r.render(tree, cam, par, image=img, accum=acc), a.repeats)
+            r.render(tree, cam, par_count, image=img, accum=acc)
             ls = r.stats()
             bms_ = timed(lambda: r.render_bruteforce(xyz, mass, h, cam, par, image=img, accum=acc), a.repeats)
+            r.render_bruteforce(xyz, mass, h, cam, par_count, image=img, accum=acc)
             bs = r.stats()
             b_bytes = 20 * p.n + W * H
             v = {"view": j, "resolution": f"{W}x{H}", "lod_p50_ms": float(np.percentile(lms, 50)),

@@ -198,8 +198,13 @@ typedef struct {
                              capped at 2^31.  A frame needing more is binned and splatted in
                              several passes over ranges of its points, with the same image */
     int32_t point_format; /* GBLOD_POINTS_*: which stored form of the octree's points is drawn */
-    int32_t reserved;     /* 0 */
+    int32_t flags;        /* GBLOD_RENDER_*: 0 or GBLOD_RENDER_COUNT_UPDATES */
 } gblod_render_params;
+
+/* Count the pixel updates of the splat ((splat, pixel) pairs inside the kernel support) into
+ * gblod_frame_stats.pixel_updates.  Instrumentation only: it does not change the image, and the
+ * splat kernel runs about 10% slower with it. */
+#define GBLOD_RENDER_COUNT_UPDATES 1
 
 /* Render workspace: scratch buffers (grown on demand through the allocator), the sticky
  * device status word and the last frame's counters.  One renderer must not be used by two
@@ -232,7 +237,8 @@ typedef struct {
     uint64_t pairs;          /* (tile, splat) records */
     uint64_t tiles;
     uint64_t amplitude_lo, amplitude_hi; /* sum of drawn amplitudes */
-    uint64_t pixel_updates;  /* (splat, pixel) pairs inside the kernel support */
+    uint64_t pixel_updates;  /* (splat, pixel) pairs inside the kernel support (0 unless the frame
+                                was rendered with GBLOD_RENDER_COUNT_UPDATES) */
     uint64_t pixel_updates_total; /* the same, summed over every frame of this renderer */
 } gblod_frame_stats;
 

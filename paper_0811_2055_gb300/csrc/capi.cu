@@ -62,7 +62,7 @@ gblod_render_params check_params(const gblod_render_params *p)
         fail(GBLOD_ERR_INVALID_ARG, "fixed tone range needs 0 < tone_lo < tone_hi < inf");
     if (q.point_format != GBLOD_POINTS_FLOAT && q.point_format != GBLOD_POINTS_BLOCK16)
         fail(GBLOD_ERR_INVALID_ARG, "unknown point_format");
-    if (q.reserved != 0) fail(GBLOD_ERR_INVALID_ARG, "render params reserved field must be 0");
+    if (q.flags & ~GBLOD_RENDER_COUNT_UPDATES) fail(GBLOD_ERR_INVALID_ARG, "unknown render flags");
     return q;
 }
 

@@ -586,7 +586,8 @@ struct SplatSmem {
     int4 A[RT];                // U, V, S, Wh = Wq >> 16
     uint4 B[RT];               // QL low, Wl = Wq & 0xFFFF, QL high, unused
     uint16_t list[RT / 32][RT]; // per warp: record | touched blocks of its strip << 8; small records
-                                // from the front, large ones from the back
+                                // touching all four blocks from the front, other small ones from the back
+    uint16_t large[RT / 32][RT]; // per warp: the same for records with QL > 2^30
 };
 
 // 16-byte global -> shared copy that bypasses registers and L1 (completes at cp_async_wait_all)
@@ -613,9 +614,11 @@ __host__ __device__ __forceinline__ int strip_height(int nbx, int nby)
     return sh;
 }
 
-// Splats records [it.y, it.z) of tile `tile` (index inside the view) of view P into img.  Each
+// Splats records [it.y, it.z) of tile `tile` (index inside the view) of view P into img; COUNT
+// adds the pixel updates to `hits`.  Each
 // lane owns one pixel column position of its warp's strip and one pixel in every block of it;
 // a record's centre offset in x and its square are computed once per strip, not once per block.
+template <bool COUNT>
 __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const uint4 it, const uint32_t tile,
                                            const Proj &P, unsigned long long *__restrict__ img, SplatSmem &sm,
                                            unsigned &hits)
@@ -650,7 +653,7 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
         hk[k] = 0u;
     }
     const int dstep = ng * 1024; // y offset between the warp's consecutive blocks, 1/256 px
-    uint16_t *lst = sm.list[warp];
+    uint16_t *lst = sm.list[warp], *lrg = sm.large[warp];
     // records reach shared memory through `raw`, copied (cp.async) one stage ahead of their use
     const uint32_t raw_addr = (uint32_t)__cvta_generic_to_shared(&sm.raw[threadIdx.x]);
     if (it.y + threadIdx.x < it.z) cp_async16(raw_addr, rec + it.y + threadIdx.x);
@@ -672,7 +675,7 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
         if (!kvalid) continue; // warp-uniform
         // records whose support reaches a pixel centre of a block of this strip: exact test
         // q_min < QL against each block's pixel-centre rectangle
-        int ns = 0, nl = 0;
+        int nf = 0, np = 0, nl = 0;
         for (int j0 = 0; j0 < nb; j0 += 32) {
             const int j = j0 + lane;
             unsigned m = 0;
@@ -693,18 +696,43 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
                     if (ex2 + (unsigned long long)(ey * ey) < QL) m |= 1u << k;
                 }
             }
-            const bool ts = m && small, tl = m && !small;
-            const uint32_t ms = __ballot_sync(0xffffffffu, ts), ml = __ballot_sync(0xffffffffu, tl);
+            const bool tf = m == 0xFu && small, tp = m && m != 0xFu && small, tl = m && !small;
+            const uint32_t mf = __ballot_sync(0xffffffffu, tf), mp = __ballot_sync(0xffffffffu, tp),
+                           ml = __ballot_sync(0xffffffffu, tl);
             const uint16_t e = (uint16_t)(j | (m << 8));
-            if (ts) lst[ns + __popc(ms & lt)] = e;
-            if (tl) lst[RT - 1 - (nl + __popc(ml & lt))] = e;
-            ns += __popc(ms);
+            if (tf) lst[nf + __popc(mf & lt)] = e;
+            if (tp) lst[RT - 1 - (np + __popc(mp & lt))] = e;
+            if (tl) lrg[nl + __popc(ml & lt)] = e;
+            nf += __popc(mf);
+            np += __popc(mp);
             nl += __popc(ml);
         }
         __syncwarp();
+        // small records touching all four blocks: no per-block test, four independent chains
+#pragma unroll 2
+        for (int i = 0; i < nf; ++i) {
+            const int j = lst[i] & 255;
+            const int4 A = sm.A[j];
+            const uint2 B = *reinterpret_cast<const uint2 *>(&sm.B[j]); // QL, Wl
+            const int dx = pxv - A.x;
+            const uint32_t dx2 = (uint32_t)(dx * dx);
+            const int dy0 = pyv0 - A.y;
+#pragma unroll
+            for (int k = 0; k < SPLAT_SLOTS; ++k) {
+                const int dy = dy0 + k * dstep;
+                const uint32_t q = dx2 + (uint32_t)(dy * dy);
+                if (q < B.x) {
+                    const uint32_t idx = __umulhi(q, (uint32_t)A.z) >> 5;
+                    const uint32_t kv = (uint32_t)sm.K[idx];
+                    acc[k] += (unsigned long long)(uint32_t)A.w * kv;
+                    acc_lo[k] += (B.y * kv) >> 16;
+                    if (COUNT) ++hk[k];
+                }
+            }
+        }
         // lanes whose pixel lies outside the tile compute too; their sums are never stored
 #pragma unroll 2
-        for (int i = 0; i < ns; ++i) {
+        for (int i = RT - np; i < RT; ++i) {
             const uint32_t e = lst[i];
             const int j = e & 255;
             const int4 A = sm.A[j];
@@ -722,12 +750,12 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
                     const uint32_t kv = (uint32_t)sm.K[idx];
                     acc[k] += (unsigned long long)(uint32_t)A.w * kv;
                     acc_lo[k] += (B.y * kv) >> 16;
-                    ++hk[k];
+                    if (COUNT) ++hk[k];
                 }
             }
         }
-        for (int i = RT - nl; i < RT; ++i) {
-            const uint32_t e = lst[i];
+        for (int i = 0; i < nl; ++i) {
+            const uint32_t e = lrg[i];
             const int j = e & 255;
             const int4 A = sm.A[j];
             const uint4 B = sm.B[j];
@@ -745,7 +773,7 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
                     const uint32_t kv = (uint32_t)sm.K[idx];
                     acc[k] += (unsigned long long)(uint32_t)A.w * kv;
                     acc_lo[k] += (B.y * kv) >> 16;
-                    ++hk[k];
+                    if (COUNT) ++hk[k];
                 }
             }
         }
@@ -754,7 +782,7 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
     for (int k = 0; k < SPLAT_SLOTS; ++k) {
         const int pyl = pyl0 + 4 * ng * k;
         if (!(kvalid >> k & 1u) || pxl >= TWc || pyl >= THc) continue;
-        hits += hk[k];
+        if (COUNT) hits += hk[k];
         const unsigned long long v = acc[k] + acc_lo[k];
         if (v) atomicAdd(&img[(size_t)(Y0 + pyl) * P.W + (X0 + pxl)], v);
     }
@@ -770,6 +798,7 @@ __device__ __forceinline__ void count_hits(unsigned hits, FrameStatsDev *stats)
     }
 }
 
+template <bool COUNT>
 __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
                                                        Proj P, unsigned long long *__restrict__ img,
                                                        FrameStatsDev *stats)
@@ -778,8 +807,8 @@ __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__
     for (int i = threadIdx.x; i < 1024; i += RT) sm.K[i] = g_ktab[P.kernel][i];
     unsigned hits = 0;
     const uint4 it = items[blockIdx.x];
-    splat_item(rec, it, it.x, P, img, sm, hits);
-    count_hits(hits, stats);
+    splat_item<COUNT>(rec, it, it.x, P, img, sm, hits);
+    if (COUNT) count_hits(hits, stats);
 }
 
 // ------------------------------------------------------------------ R4
@@ -897,8 +926,8 @@ void bin_splat(gblod_renderer *r, const Src &src, const Proj &P, unsigned long l
     launch(GBLOD_K_RENDER_OTHER, k_fill_items, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
            (const uint32_t *)r->tile_cnt.p, (const uint32_t *)r->tile_off.p, (const uint32_t *)r->item_off.p,
            r->items.p);
-    launch(GBLOD_K_SPLAT, k_splat_tiles, dim3(pc.items), dim3(RT), 0, s, (const uint4 *)r->records.p,
-           (const uint4 *)r->items.p, P, img, r->stats);
+    launch(GBLOD_K_SPLAT, r->count_updates ? k_splat_tiles<true> : k_splat_tiles<false>, dim3(pc.items), dim3(RT), 0,
+           s, (const uint4 *)r->records.p, (const uint4 *)r->items.p, P, img, r->stats);
 }
 
 template <class Src>
@@ -907,6 +936,7 @@ void frame_common(gblod_renderer *r, const Src &src, const Proj &P, const gblod_
 {
     const Allocator &A = r->A;
     const uint32_t ntiles = (uint32_t)(P.tiles_x * P.tiles_y);
+    r->count_updates = (rp.flags & GBLOD_RENDER_COUNT_UPDATES) != 0;
     r->tile_cnt.ensure(A, ntiles, s);
     r->tile_off.ensure(A, ntiles + 1, s);
     r->tile_cur.ensure(A, ntiles, s);
@@ -1250,6 +1280,7 @@ __global__ void k_bfill_items(uint32_t ntiles, const ViewDev *__restrict__ views
     }
 }
 
+template <bool COUNT>
 __global__ void __launch_bounds__(RT, 4) k_bsplat(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
                                                   const uint32_t *nitems_p, uint32_t items_cap,
                                                   const ViewDev *__restrict__ views, unsigned *next_item,
@@ -1275,9 +1306,9 @@ __global__ void __launch_bounds__(RT, 4) k_bsplat(const uint4 *__restrict__ rec,
             for (int j = threadIdx.x; j < 1024; j += RT) sm.K[j] = g_ktab[P.kernel][j];
             kernel_loaded = P.kernel;
         }
-        splat_item(rec, it, it.x, P, views[it.w].accum, sm, hits);
+        splat_item<COUNT>(rec, it, it.x, P, views[it.w].accum, sm, hits);
     }
-    count_hits(hits, stats);
+    if (COUNT) count_hits(hits, stats);
 }
 
 // R4 over the views of a batch: blockIdx.y = view, grid-stride over that view's pixels
@@ -1475,7 +1506,8 @@ void render_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod
            (const uint32_t *)r->item_off.p, r->items.p, (uint32_t)items_cap, (unsigned long long)r->b_rec_cap,
            (const FrameStatsDev *)r->stats, r->status);
     // R3: persistent over the items of all views
-    launch(GBLOD_K_SPLAT, k_bsplat, dim3(G), dim3(RT), 0, s, (const uint4 *)r->records.p, (const uint4 *)r->items.p,
+    launch(GBLOD_K_SPLAT, (rp.flags & GBLOD_RENDER_COUNT_UPDATES) ? k_bsplat<true> : k_bsplat<false>, dim3(G), dim3(RT),
+           0, s, (const uint4 *)r->records.p, (const uint4 *)r->items.p,
            (const uint32_t *)(r->item_off.p + b.ntiles), (uint32_t)items_cap, (const ViewDev *)dv,
            r->lvl_cnt.p + b.max_levels + 2, r->stats);
     // R4
@@ -1740,8 +1772,8 @@ gblod_status render_brute_noalloc(const float *xyz, const float *mass, const flo
     const size_t npix = (size_t)P.W * P.H;
     unsigned long long *img = reinterpret_cast<unsigned long long *>(accum);
     GB_CUDA(cudaMemsetAsync(img, 0, npix * 8, s));
-    launch(GBLOD_K_SPLAT, k_splat_tiles, dim3(nitems), dim3(RT), 0, s, (const uint4 *)records, (const uint4 *)items,
-           P, img, stats);
+    launch(GBLOD_K_SPLAT, (rp.flags & GBLOD_RENDER_COUNT_UPDATES) ? k_splat_tiles<true> : k_splat_tiles<false>,
+           dim3(nitems), dim3(RT), 0, s, (const uint4 *)records, (const uint4 *)items, P, img, stats);
     if (image) {
         double lo = 0.0, hi = 0.0;
         if (rp.tone_auto) {

@@ -17,6 +17,7 @@ struct gblod_renderer {
     gb::ScanTmp scan;
     unsigned *status = nullptr;             // sticky device status bits
     gb::FrameStatsDev *stats = nullptr;     // device counters of the last frame
+    bool count_updates = false;             // this frame counts its pixel updates
     // R1
     gb::DBuf<uint32_t> frontA, frontB, sel, lvl_cnt;
     gb::DBuf<uint64_t> sel_pfx;

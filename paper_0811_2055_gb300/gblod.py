@@ -20,6 +20,7 @@ OK, ERR_INVALID_ARG, ERR_RANGE, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_NOT_I
 NODE_LEAF, NODE_INTERNAL, NODE_LOSSY, NODE_REPS = 1, 2, 4, 8
 KERNEL_GAUSSIAN, KERNEL_CUBIC = 0, 1
 POINTS_FLOAT, POINTS_BLOCK16 = 0, 1
+RENDER_COUNT_UPDATES = 1
 QUANTIZE_DROP_FLOAT = 1
 (K_ANY, K_MORTON, K_SORT_UPSWEEP, K_SORT_SCATTER, K_SCAN, K_BUILD_OTHER, K_SEL_HIST, K_SEL_MARK, K_SEL_WRITE,
  K_SELECT_NODES, K_PROJECT_COUNT, K_PROJECT_SCATTER, K_SPLAT, K_TONEMAP, K_RENDER_OTHER) = range(15)
@@ -49,7 +50,7 @@ class RenderParams(C.Structure):
     _fields_ = [("lambda_px", C.c_double), ("sigma_min_px", C.c_double), ("sigma_max_px", C.c_double),
                 ("tone_lo", C.c_double), ("tone_hi", C.c_double), ("kernel", C.c_int32),
                 ("tone_auto", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
-                ("record_budget", C.c_uint64), ("point_format", C.c_int32), ("reserved", C.c_int32)]
+                ("record_budget", C.c_uint64), ("point_format", C.c_int32), ("flags", C.c_int32)]
 
 
 class View(C.Structure):
@@ -155,7 +156,7 @@ def make_camera(cam: dict) -> Camera:
 
 def make_params(lambda_px=None, sigma_min_px=0.5, sigma_max_px=128.0, kernel=KERNEL_GAUSSIAN, tone_auto=True,
                 tone_lo=0.0, tone_hi=0.0, tile_w=0, tile_h=0, record_budget=0,
-                point_format=POINTS_FLOAT) -> RenderParams:
+                point_format=POINTS_FLOAT, count_updates=False) -> RenderParams:
     p = RenderParams()
     p.lambda_px = -1.0 if lambda_px is None else float(lambda_px)
     p.sigma_min_px, p.sigma_max_px = float(sigma_min_px), float(sigma_max_px)
@@ -164,6 +165,7 @@ def make_params(lambda_px=None, sigma_min_px=0.5, sigma_max_px=128.0, kernel=KER
     p.tile_w, p.tile_h = int(tile_w), int(tile_h)
     p.record_budget = int(record_budget)
     p.point_format = int(point_format)
+    p.flags = RENDER_COUNT_UPDATES if count_updates else 0
     return p
 
 

@@ -112,6 +112,20 @@ def test_tiling_does_not_change_the_image(G, R, tile):
     assert torch.equal(a, b)
 
 
+def test_counting_pixel_updates_keeps_the_image(G, R):
+    p = synth.tiny(30000, seed=25)
+    cam = _cams()["inside"]
+    t = G.build_lod(*to_dev(p.xyz, p.mass, p.h), n_max=300, seed=2)
+    _, a = R.render(t, cam, G.make_params())
+    assert R.stats()["pixel_updates"] == 0
+    _, b = R.render(t, cam, G.make_params(count_updates=True))
+    n = R.stats()["pixel_updates"]
+    assert torch.equal(a, b) and n > 0
+    # the same frame counted by the tile shape that evaluates other pixel blocks gives the same count
+    _, c = R.render(t, cam, G.make_params(count_updates=True, tile_w=16, tile_h=16))
+    assert torch.equal(a, c) and R.stats()["pixel_updates"] == n
+
+
 @pytest.mark.parametrize("parts", [3, 17, 150])
 def test_split_frames_give_the_same_image(G, R, parts):
     """A frame whose records exceed the budget is binned in several passes: same image."""
