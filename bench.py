@@ -466,6 +466,13 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def splat_source(src: bytes) -> bytes:
+    """The splat kernel's source: render.cu from `struct SplatSmem` to the end of `k_splat_tiles`."""
+    a = src.index(b"struct SplatSmem {")
+    b = src.index(b"\n}\n", src.index(b"k_splat_tiles(", a)) + 3
+    return src[a:b]
+
+
 def splat_traffic(a, lod_counts, nf):
     """DRAM bytes per splat launch from the committed ncu summary, if it was taken of this kernel source."""
     import hashlib
@@ -476,10 +483,10 @@ def splat_traffic(a, lod_counts, nf):
         src = open(os.path.join(root, "paper_0811_2055_gb300", "csrc", "render.cu"), "rb").read()
     except OSError:
         return None
-    m = re.search(r"render\.cu sha256: ([0-9a-f]{64})", prof)
+    m = re.search(r"splat kernel source sha256: ([0-9a-f]{64})", prof)
     rd = re.search(r"`dram__bytes_read\.sum` \| ([0-9.]+) Mbyte", prof)
     wr = re.search(r"`dram__bytes_write\.sum` \| ([0-9.]+) Mbyte", prof)
-    if not (m and rd and wr) or m.group(1) != hashlib.sha256(src).hexdigest():
+    if not (m and rd and wr) or m.group(1) != hashlib.sha256(splat_source(src)).hexdigest():
         return None
     if a.workload != "mid" or a.particles or not lod_counts["pairs_first"]:
         return None

@@ -192,7 +192,7 @@ typedef struct {
     int32_t kernel;       /* GBLOD_KERNEL_* */
     int32_t tone_auto;    /* 1: hi = image maximum, lo = 1e-4 hi */
     int32_t tile_w, tile_h; /* screen tile, 1..64 each, covering at most 8 strips of 8 x 16
-                             pixels (ceil(w/8) ceil(h/16) <= 8; 0 = 32); any value gives the
+                             pixels (ceil(w/8) ceil(h/16) <= 8; 0 = 64 wide, 16 high); any value gives the
                              same image */
     uint64_t record_budget; /* most (tile, splat) records held at once (16 bytes each); 0 = 2^28,
                              capped at 2^31.  A frame needing more is binned and splatted in
@@ -333,7 +333,7 @@ gblod_status gblod_diff_backward(gblod_renderer *r, const float *d_xyz, const fl
  *   - the first call on a device also performs that device's set-up (resolves the array's device
  *     address and uploads the kernel table); make that first call before any stream capture;
  *   - frames are limited to GBLOD_NOALLOC_MAX_TILES screen tiles (e.g. 4096 x 4096 pixels with
- *     the default 32 x 32 tiles; larger images are rejected with GBLOD_ERR_INVALID_ARG) and to
+ *     the default 64 x 16 tiles; larger images are rejected with GBLOD_ERR_INVALID_ARG) and to
  *     GBLOD_NOALLOC_MAX_RECORDS (tile, splat) records (a frame that needs more returns
  *     GBLOD_ERR_RANGE before anything is splatted; d_accum is then left unspecified);
  *   - every call shares the one array, so calls that overlap on the GPU (on different streams, or
@@ -341,7 +341,7 @@ gblod_status gblod_diff_backward(gblod_renderer *r, const float *d_xyz, const fl
  *   - the fixed-point range checks are returned directly (GBLOD_ERR_RANGE) since there is no
  *     renderer object to hold a status word; the frame is still completed without the dropped
  *     splats.  The call waits once on `stream` mid-frame, like gblod_render_bruteforce. */
-#define GBLOD_NOALLOC_MAX_TILES 16384u /* e.g. 4096 x 4096 pixels with the default 32 x 32 tiles */
+#define GBLOD_NOALLOC_MAX_TILES 16384u /* e.g. 4096 x 4096 pixels with the default 64 x 16 tiles */
 #define GBLOD_NOALLOC_MAX_RECORDS 2097152u
 #define GBLOD_NOALLOC_SCRATCH_BYTES 34227456u /* 32.6 MiB */
 gblod_status gblod_render_bruteforce_noalloc(const float *d_xyz, const float *d_mass, const float *d_h, uint64_t n,

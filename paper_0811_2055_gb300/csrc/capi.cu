@@ -53,8 +53,8 @@ gblod_render_params check_params(const gblod_render_params *p)
     if (q.kernel != GBLOD_KERNEL_GAUSSIAN && q.kernel != GBLOD_KERNEL_CUBIC)
         fail(GBLOD_ERR_INVALID_ARG, "unknown kernel");
     if (std::isnan(q.lambda_px)) fail(GBLOD_ERR_INVALID_ARG, "lambda_px is NaN");
-    if (q.tile_w == 0) q.tile_w = 32;
-    if (q.tile_h == 0) q.tile_h = 32;
+    if (q.tile_w == 0) q.tile_w = 64;
+    if (q.tile_h == 0) q.tile_h = 16;
     if (q.tile_w < 1 || q.tile_h < 1 || q.tile_w > 64 || q.tile_h > 64 ||
         ((q.tile_w + 7) / 8) * ((q.tile_h + 15) / 16) > 8)
         fail(GBLOD_ERR_INVALID_ARG, "tile must be 1..64 x 1..64 with ceil(w/8) ceil(h/16) <= 8 (8 strips of 8 x 16 pixels)");

@@ -102,8 +102,8 @@ Proj make_proj(const gblod_camera &c, const gblod_render_params &rp)
     P.Hf = (float)c.height;
     P.W = c.width;
     P.H = c.height;
-    P.TW = rp.tile_w > 0 ? rp.tile_w : 32;
-    P.TH = rp.tile_h > 0 ? rp.tile_h : 32;
+    P.TW = rp.tile_w > 0 ? rp.tile_w : 64;
+    P.TH = rp.tile_h > 0 ? rp.tile_h : 16;
     P.tiles_x = (P.W + P.TW - 1) / P.TW;
     P.tiles_y = (P.H + P.TH - 1) / P.TH;
     P.kernel = cubic ? 1 : 0;
@@ -452,6 +452,56 @@ struct AmpSum {
     }
 };
 
+// Warp-cooperative scatter of (splat, tile) records.  Lane l contributes n_l pairs: the tiles
+// t00_l + row * tiles_x_l + col of its box, row < n_l / tw_l, col < tw_l (n_l = 0: none).  The warp
+// walks the concatenation of all lanes' pairs 32 at a time, so one lane with many tiles does not
+// hold the others idle; pairs of one round that share a tile reserve their slots from cursor[t]
+// with one atomic (match_any) and write the source lane's record r (slots at or past rec_cap are
+// dropped).
+__device__ __forceinline__ void scatter_pairs(uint32_t n, uint32_t t00, int tw, int tiles_x, const uint4 r,
+                                              uint32_t *__restrict__ cursor, uint4 *__restrict__ rec,
+                                              unsigned long long rec_cap)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = gbd::lanemask_lt();
+    uint32_t incl = n;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += o;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t excl = incl - n;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t k = base + (uint32_t)lane;
+        int src = 0; // the last lane whose pairs start at or before k
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t ex = __shfl_sync(0xffffffffu, excl, src + step);
+            if (ex <= k) src += step;
+        }
+        const uint32_t m = k - __shfl_sync(0xffffffffu, excl, src);
+        const uint32_t st00 = __shfl_sync(0xffffffffu, t00, src);
+        const int stw = __shfl_sync(0xffffffffu, tw, src), stx = __shfl_sync(0xffffffffu, tiles_x, src);
+        uint4 sr;
+        sr.x = __shfl_sync(0xffffffffu, r.x, src);
+        sr.y = __shfl_sync(0xffffffffu, r.y, src);
+        sr.z = __shfl_sync(0xffffffffu, r.z, src);
+        sr.w = __shfl_sync(0xffffffffu, r.w, src);
+        const bool act = k < total;
+        const uint32_t amask = __ballot_sync(0xffffffffu, act);
+        if (act) {
+            const uint32_t row = m / (uint32_t)stw, col = m - row * (uint32_t)stw;
+            const uint32_t t = st00 + row * (uint32_t)stx + col;
+            const uint32_t peers = __match_any_sync(amask, t);
+            const int leader = __ffs(peers) - 1;
+            uint32_t b = 0;
+            if (lane == leader) b = atomicAdd(&cursor[t], (uint32_t)__popc(peers));
+            b = __shfl_sync(peers, b, leader);
+            const unsigned long long pos = (unsigned long long)b + __popc(peers & lt);
+            if (pos < rec_cap) rec[pos] = sr;
+        }
+    }
+}
+
 template <class Src>
 __global__ void __launch_bounds__(RT) k_project_count(Src src, Proj P, unsigned long long e_lo,
                                                       unsigned long long e_hi, uint32_t *__restrict__ tile_cnt,
@@ -511,8 +561,6 @@ __global__ void __launch_bounds__(RT) k_project_scatter(Src src, Proj P, unsigne
                                                         uint4 *__restrict__ rec)
 {
     const unsigned long long total = min(src_total(src), e_hi);
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt = gbd::lanemask_lt();
     for (unsigned long long a = e_lo + (unsigned long long)blockIdx.x * CHUNK; a < total;
          a += (unsigned long long)gridDim.x * CHUNK) {
         const unsigned long long b = min(total, a + CHUNK);
@@ -527,25 +575,21 @@ __global__ void __launch_bounds__(RT) k_project_scatter(Src src, Proj P, unsigne
                 src_load(src, e, j0, j1, x, y, z, w, h);
                 res = project(P, x, y, z, w, h, s);
             }
+            uint32_t n = 0, t00 = 0;
+            int tw = 1;
+            uint4 r = make_uint4(0u, 0u, 0u, 0u);
             if (res == 1) {
                 int x0, x1, y0, y1;
                 splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
                 if (x0 <= x1 && y0 <= y1) {
-                    const uint4 r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
+                    r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
                     const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
-                    for (int ty = ty0; ty <= ty1; ++ty)
-                        for (int tx = tx0; tx <= tx1; ++tx) {
-                            const uint32_t t = (uint32_t)(ty * P.tiles_x + tx);
-                            const uint32_t mask = __activemask();
-                            const uint32_t peers = __match_any_sync(mask, t);
-                            const int leader = __ffs(peers) - 1;
-                            uint32_t base = 0;
-                            if (lane == leader) base = atomicAdd(&cursor[t], (uint32_t)__popc(peers));
-                            base = __shfl_sync(peers, base, leader);
-                            rec[base + __popc(peers & lt)] = r;
-                        }
+                    tw = tx1 - tx0 + 1;
+                    n = (uint32_t)(tw * (ty1 - ty0 + 1));
+                    t00 = (uint32_t)(ty0 * P.tiles_x + tx0);
                 }
             }
+            scatter_pairs(n, t00, tw, P.tiles_x, r, cursor, rec, ~0ull);
         }
     }
 }
@@ -580,15 +624,18 @@ __global__ void k_fill_items(uint32_t ntiles, const uint32_t *tile_cnt, const ui
 constexpr int SPLAT_SLOTS = 4; // 8 warps x 4 blocks of 32 pixels: tiles up to 1024 pixels
 static_assert(ITEM <= (1u << 15), "32-bit partial sums need at most 2^15 records per item");
 
+constexpr int STAGE = 512; // records staged in shared memory at a time
+
 struct SplatSmem {
     int32_t K[1024];
-    uint4 raw[RT];             // records of the next stage, copied asynchronously
-    int4 A[RT];                // U, V, S, Wh = Wq >> 16
-    uint4 B[RT];               // QL low, Wl = Wq & 0xFFFF, QL high, unused
-    uint16_t list[RT / 32][RT]; // per warp: record | touched blocks of its strip << 8; small records
-                                // touching all four blocks from the front, other small ones from the back
-    uint16_t large[RT / 32][RT]; // per warp: the same for records with QL > 2^30
+    uint4 raw[STAGE];             // records of the next stage, copied asynchronously
+    int4 A[STAGE];                // U, V, S, Wh = Wq >> 16
+    uint4 B[STAGE];               // QL low, Wl = Wq & 0xFFFF, QL high, unused
+    uint16_t list[RT / 32][STAGE]; // per warp: record | touched blocks of its column << 9; small records
+                                   // touching all four blocks from the front, other small ones from the back
+    uint16_t large[RT / 32][STAGE]; // per warp: the same for records with QL > 2^30
 };
+static_assert(sizeof(SplatSmem) <= 48 * 1024, "static shared memory limit");
 
 // 16-byte global -> shared copy that bypasses registers and L1 (completes at cp_async_wait_all)
 __device__ __forceinline__ void cp_async16(uint32_t smem_addr, const uint4 *g)
@@ -656,21 +703,24 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
     uint16_t *lst = sm.list[warp], *lrg = sm.large[warp];
     // records reach shared memory through `raw`, copied (cp.async) one stage ahead of their use
     const uint32_t raw_addr = (uint32_t)__cvta_generic_to_shared(&sm.raw[threadIdx.x]);
-    if (it.y + threadIdx.x < it.z) cp_async16(raw_addr, rec + it.y + threadIdx.x);
+    for (int t = threadIdx.x; t < STAGE; t += RT)
+        if (it.y + t < it.z) cp_async16(raw_addr + 16u * (uint32_t)(t - threadIdx.x), rec + it.y + t);
     cp_async_commit();
-    for (uint32_t base = it.y; base < it.z; base += RT) {
+    for (uint32_t base = it.y; base < it.z; base += STAGE) {
         cp_async_wait_all();
         __syncthreads();
-        const int nb = (int)min((uint32_t)RT, it.z - base);
-        if ((int)threadIdx.x < nb) {
-            const uint4 R = sm.raw[threadIdx.x];
+        const int nb = (int)min((uint32_t)STAGE, it.z - base);
+        for (int t = threadIdx.x; t < nb; t += RT) {
+            const uint4 R = sm.raw[t];
             const unsigned long long Wq = __float2ull_rn(__uint_as_float(R.w));
             const unsigned long long QL = 140737488355327ull / (unsigned long long)R.z + 1ull;
-            sm.A[threadIdx.x] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)(Wq >> 16));
-            sm.B[threadIdx.x] = make_uint4((uint32_t)QL, (uint32_t)(Wq & 0xFFFFull), (uint32_t)(QL >> 32), 0u);
+            sm.A[t] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)(Wq >> 16));
+            sm.B[t] = make_uint4((uint32_t)QL, (uint32_t)(Wq & 0xFFFFull), (uint32_t)(QL >> 32), 0u);
         }
         __syncthreads();
-        if (base + RT + threadIdx.x < it.z) cp_async16(raw_addr, rec + base + RT + threadIdx.x);
+        for (int t = threadIdx.x; t < STAGE; t += RT)
+            if (base + STAGE + t < it.z)
+                cp_async16(raw_addr + 16u * (uint32_t)(t - threadIdx.x), rec + base + STAGE + t);
         cp_async_commit();
         if (!kvalid) continue; // warp-uniform
         // records whose support reaches a pixel centre of a block of this strip: exact test
@@ -699,9 +749,9 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
             const bool tf = m == 0xFu && small, tp = m && m != 0xFu && small, tl = m && !small;
             const uint32_t mf = __ballot_sync(0xffffffffu, tf), mp = __ballot_sync(0xffffffffu, tp),
                            ml = __ballot_sync(0xffffffffu, tl);
-            const uint16_t e = (uint16_t)(j | (m << 8));
+            const uint16_t e = (uint16_t)(j | (m << 9));
             if (tf) lst[nf + __popc(mf & lt)] = e;
-            if (tp) lst[RT - 1 - (np + __popc(mp & lt))] = e;
+            if (tp) lst[STAGE - 1 - (np + __popc(mp & lt))] = e;
             if (tl) lrg[nl + __popc(ml & lt)] = e;
             nf += __popc(mf);
             np += __popc(mp);
@@ -711,7 +761,7 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
         // small records touching all four blocks: no per-block test, four independent chains
 #pragma unroll 2
         for (int i = 0; i < nf; ++i) {
-            const int j = lst[i] & 255;
+            const int j = lst[i] & 511;
             const int4 A = sm.A[j];
             const uint2 B = *reinterpret_cast<const uint2 *>(&sm.B[j]); // QL, Wl
             const int dx = pxv - A.x;
@@ -732,9 +782,9 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
         }
         // lanes whose pixel lies outside the tile compute too; their sums are never stored
 #pragma unroll 2
-        for (int i = RT - np; i < RT; ++i) {
+        for (int i = STAGE - np; i < STAGE; ++i) {
             const uint32_t e = lst[i];
-            const int j = e & 255;
+            const int j = e & 511;
             const int4 A = sm.A[j];
             const uint2 B = *reinterpret_cast<const uint2 *>(&sm.B[j]); // QL, Wl
             const int dx = pxv - A.x;
@@ -742,7 +792,7 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
             const int dy0 = pyv0 - A.y;
 #pragma unroll
             for (int k = 0; k < SPLAT_SLOTS; ++k) {
-                if (!(e >> (8 + k) & 1u)) continue; // warp-uniform
+                if (!(e >> (9 + k) & 1u)) continue; // warp-uniform
                 const int dy = dy0 + k * dstep;
                 const uint32_t q = dx2 + (uint32_t)(dy * dy);
                 if (q < B.x) {
@@ -756,7 +806,7 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
         }
         for (int i = 0; i < nl; ++i) {
             const uint32_t e = lrg[i];
-            const int j = e & 255;
+            const int j = e & 511;
             const int4 A = sm.A[j];
             const uint4 B = sm.B[j];
             const unsigned long long QL = ((unsigned long long)B.z << 32) | B.x;
@@ -765,7 +815,7 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
             const int dy0 = pyv0 - A.y;
 #pragma unroll
             for (int k = 0; k < SPLAT_SLOTS; ++k) {
-                if (!(e >> (8 + k) & 1u)) continue;
+                if (!(e >> (9 + k) & 1u)) continue;
                 const int dy = dy0 + k * dstep;
                 const unsigned long long q = (unsigned long long)(dx2 + (long long)dy * dy);
                 if (q < QL) {
@@ -1214,6 +1264,9 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
                 if (__any_sync(0xffffffffu, res < 0) && lane == 0) atomicOr(status, ST_RANGE);
                 if (res == 1) amp.add(__float2ull_rn(s.Wf));
             }
+            uint32_t n = 0, t00 = 0;
+            int tw = 1, tiles_x = 1;
+            uint4 r = make_uint4(0u, 0u, 0u, 0u);
             if (res == 1) {
                 const Proj &P = v == sV[0] ? sP[0] : (v == sV[1] ? sP[1] : src.views[v].P);
                 const uint32_t tb = src.views[v].tile_base;
@@ -1222,24 +1275,24 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
                 splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
                 if (x0 <= x1 && y0 <= y1) {
                     const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
-                    if (!SCATTER) pairs += (unsigned long long)(tx1 - tx0 + 1) * (unsigned long long)(ty1 - ty0 + 1);
-                    const uint4 r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
-                    for (int ty = ty0; ty <= ty1; ++ty)
-                        for (int tx = tx0; tx <= tx1; ++tx) {
-                            const uint32_t t = tb + (uint32_t)(ty * P.tiles_x + tx);
-                            const uint32_t mask = __activemask();
-                            const uint32_t peers = __match_any_sync(mask, t);
-                            const int leader = __ffs(peers) - 1;
-                            if (!SCATTER) {
-                                if (lane == leader) atomicAdd(&tile_cnt[t], (uint32_t)__popc(peers));
-                            } else {
-                                uint32_t base = 0;
-                                if (lane == leader) base = atomicAdd(&cursor[t], (uint32_t)__popc(peers));
-                                base = __shfl_sync(peers, base, leader);
-                                const unsigned long long pos = (unsigned long long)base + __popc(peers & lt);
-                                if (pos < rec_cap) rec[pos] = r;
-                            }
-                        }
+                    tw = tx1 - tx0 + 1;
+                    n = (uint32_t)(tw * (ty1 - ty0 + 1));
+                    t00 = tb + (uint32_t)(ty0 * P.tiles_x + tx0);
+                    tiles_x = P.tiles_x;
+                    if (!SCATTER) pairs += n;
+                    r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
+                }
+            }
+            if (SCATTER) {
+                scatter_pairs(n, t00, tw, tiles_x, r, cursor, rec, rec_cap);
+            } else if (n) {
+                // counting: fire-and-forget atomics, so the per-lane loop is cheaper than the
+                // warp-cooperative walk
+                for (uint32_t m = 0; m < n; ++m) {
+                    const uint32_t row = m / (uint32_t)tw;
+                    const uint32_t t = t00 + row * (uint32_t)tiles_x + (m - row * (uint32_t)tw);
+                    const uint32_t peers = __match_any_sync(__activemask(), t);
+                    if (lane == __ffs(peers) - 1) atomicAdd(&tile_cnt[t], (uint32_t)__popc(peers));
                 }
             }
         }

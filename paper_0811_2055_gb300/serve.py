@@ -19,7 +19,6 @@ frame requests are rendered by continuous batching:
 from __future__ import annotations
 
 import dataclasses
-import heapq
 import math
 import time
 

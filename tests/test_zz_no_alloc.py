@@ -11,7 +11,6 @@ torch allocation happens during the calls.  Runs alone or after the other tests.
 """
 import ctypes as C
 
-import numpy as np
 import pytest
 import torch
 
@@ -68,7 +67,7 @@ def test_noalloc_rejects_frames_beyond_its_maximum():
     f = _entry(gblod.lib())
     p = synth.uniform(100, seed=2)
     xyz, mass, h = (torch.from_numpy(a).to(dev) for a in (p.xyz, p.mass, p.h))
-    cam = synth.look_at((0.5, 0.5, -1.0), (0.5, 0.5, 0.5), width=8192, height=8192)  # 65,536 tiles of 32x32
+    cam = synth.look_at((0.5, 0.5, -1.0), (0.5, 0.5, 0.5), width=8192, height=8192)  # 65,536 tiles of 64x16
     acc = torch.zeros((16, 16), dtype=torch.int64, device=dev)
     c, params = gblod.make_camera(cam), gblod.make_params()
     st = f(xyz.data_ptr(), mass.data_ptr(), h.data_ptr(), p.n, C.addressof(c), C.addressof(params), None,
