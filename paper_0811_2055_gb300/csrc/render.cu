@@ -624,7 +624,7 @@ __global__ void k_fill_items(uint32_t ntiles, const uint32_t *tile_cnt, const ui
 constexpr int SPLAT_SLOTS = 4; // 8 warps x 4 blocks of 32 pixels: tiles up to 1024 pixels
 static_assert(ITEM <= (1u << 15), "32-bit partial sums need at most 2^15 records per item");
 
-constexpr int STAGE = 512; // records staged in shared memory at a time
+constexpr int STAGE = 384; // records staged in shared memory at a time
 
 struct SplatSmem {
     int32_t K[1024];
@@ -634,6 +634,8 @@ struct SplatSmem {
     uint16_t list[RT / 32][STAGE]; // per warp: record | touched blocks of its column << 9; small records
                                    // touching all four blocks from the front, other small ones from the back
     uint16_t large[RT / 32][STAGE]; // per warp: the same for records with QL > 2^30
+    uint16_t cand[8][STAGE];       // per block column: records whose support may reach it
+    uint32_t ncand[2][8];          // candidate counts, two sets used on alternate stages
 };
 static_assert(sizeof(SplatSmem) <= 48 * 1024, "static shared memory limit");
 
@@ -706,9 +708,13 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
     for (int t = threadIdx.x; t < STAGE; t += RT)
         if (it.y + t < it.z) cp_async16(raw_addr + 16u * (uint32_t)(t - threadIdx.x), rec + it.y + t);
     cp_async_commit();
-    for (uint32_t base = it.y; base < it.z; base += STAGE) {
+    if (threadIdx.x < 16) sm.ncand[threadIdx.x >> 3][threadIdx.x & 7] = 0u;
+    int par = 0;
+    for (uint32_t base = it.y; base < it.z; base += STAGE, par ^= 1) {
         cp_async_wait_all();
         __syncthreads();
+        // the other set of counts was last read two stages ago: clear it for the next stage
+        if (threadIdx.x < 8) sm.ncand[par ^ 1][threadIdx.x] = 0u;
         const int nb = (int)min((uint32_t)STAGE, it.z - base);
         for (int t = threadIdx.x; t < nb; t += RT) {
             const uint4 R = sm.raw[t];
@@ -716,6 +722,13 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
             const unsigned long long QL = 140737488355327ull / (unsigned long long)R.z + 1ull;
             sm.A[t] = make_int4((int)R.x, (int)R.y, (int)R.z, (int)(uint32_t)(Wq >> 16));
             sm.B[t] = make_uint4((uint32_t)QL, (uint32_t)(Wq & 0xFFFFull), (uint32_t)(QL >> 32), 0u);
+            // block columns whose pixel centres may lie inside the support (|x - U| < sqrt(QL),
+            // rounded up): a superset of the columns the exact per-block test can accept
+            const int rq = (int)sqrtf((float)QL) + 2;
+            const int lx0 = ((int)R.x - 128 - rq) >> 8, lx1 = ((int)R.x - 128 + rq) >> 8; // floor
+            const int c0 = max(0, lx0 - X0) >> 3, c1 = min(TWc - 1, lx1 - X0) >> 3;
+            if (lx1 - X0 >= 0)
+                for (int c = c0; c <= c1; ++c) sm.cand[c][atomicAdd(&sm.ncand[par][c], 1u)] = (uint16_t)t;
         }
         __syncthreads();
         for (int t = threadIdx.x; t < STAGE; t += RT)
@@ -726,11 +739,12 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
         // records whose support reaches a pixel centre of a block of this strip: exact test
         // q_min < QL against each block's pixel-centre rectangle
         int nf = 0, np = 0, nl = 0;
-        for (int j0 = 0; j0 < nb; j0 += 32) {
-            const int j = j0 + lane;
+        const int nc = (int)sm.ncand[par][scol];
+        for (int j0 = 0; j0 < nc; j0 += 32) {
+            const int j = j0 + lane < nc ? sm.cand[scol][j0 + lane] : 0;
             unsigned m = 0;
             bool small = false;
-            if (j < nb) {
+            if (j0 + lane < nc) {
                 const int4 A = sm.A[j];
                 const uint4 B = sm.B[j];
                 const unsigned long long QL = ((unsigned long long)B.z << 32) | B.x;
