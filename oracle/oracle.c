@@ -744,7 +744,9 @@ int orc_project(const orc_camera *c, const orc_rparams *rp, float x, float y, fl
 /* Adds one splat into the W x H accumulator: every pixel centre (256 px + 128, 256 py + 128)
  * gets floor(Wq K[i] / 2^16) where i = (q S) >> 37 and q is the squared distance in 1/256 px,
  * provided i < 1024.  The pixel loop covers a generous box; the table test decides. */
-static void orc_splat_one(const orc_proj *P, const orc_splat *s, int W, int H, uint64_t *acc)
+/* Adds one splat to acc (if acc != NULL) and counts its pixel updates, the (splat, pixel) pairs
+ * with a table index below 1024, into *updates (if updates != NULL). */
+static void orc_splat_one(const orc_proj *P, const orc_splat *s, int W, int H, uint64_t *acc, uint64_t *updates)
 {
     /* support radius in 1/256 px: q S < 1024 * 2^37 needs q < 2^47 / S */
     double qlim = 140737488355328.0 / (double)s->S;
@@ -764,7 +766,8 @@ static void orc_splat_one(const orc_proj *P, const orc_splat *s, int W, int H, u
             u128 idx = qs >> 37;
             if (idx < ORC_T) {
                 u128 c = ((u128)s->Wq * (u128)(uint32_t)P->K[(int)idx]) >> 16;
-                acc[py * W + px] += (uint64_t)c;
+                if (acc) acc[py * W + px] += (uint64_t)c;
+                if (updates) ++*updates;
             }
         }
     }
@@ -789,7 +792,7 @@ int orc_splat_points(const float *pts4, const float *hs, uint64_t n, const orc_c
         if (r != 1) continue;
         total += s.Wq;
         drawn++;
-        orc_splat_one(&P, &s, c->width, c->height, acc);
+        orc_splat_one(&P, &s, c->width, c->height, acc, NULL);
     }
     if (total >> 64) st = ORC_ERR_RANGE;
     if (n_drawn) *n_drawn = drawn;
@@ -797,6 +800,21 @@ int orc_splat_points(const float *pts4, const float *hs, uint64_t n, const orc_c
 }
 
 /* Same, from the input layout: xyz rows, mass, h. */
+/* Pixel updates of drawing these points: the number of (splat, pixel) pairs inside the support. */
+uint64_t orc_count_updates(const float *pts4, const float *hs, uint64_t n, const orc_camera *c, const orc_rparams *rp)
+{
+    orc_proj P;
+    orc_proj_init(&P, c, rp);
+    uint64_t updates = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        orc_splat s;
+        if (orc_project_one(&P, pts4[4 * i], pts4[4 * i + 1], pts4[4 * i + 2], pts4[4 * i + 3], hs[i], &s) != 1)
+            continue;
+        orc_splat_one(&P, &s, c->width, c->height, NULL, &updates);
+    }
+    return updates;
+}
+
 int orc_splat_particles(const float *xyz, const float *mass, const float *h, uint64_t n, const orc_camera *c,
                         const orc_rparams *rp, uint64_t *acc, uint64_t *n_drawn)
 {
@@ -812,7 +830,7 @@ int orc_splat_particles(const float *xyz, const float *mass, const float *h, uin
         if (r != 1) continue;
         total += s.Wq;
         drawn++;
-        orc_splat_one(&P, &s, c->width, c->height, acc);
+        orc_splat_one(&P, &s, c->width, c->height, acc, NULL);
     }
     if (total >> 64) st = ORC_ERR_RANGE;
     if (n_drawn) *n_drawn = drawn;
@@ -977,7 +995,7 @@ int orc_render_lod(const orc_tree *T, const double lo[3], double side, const orc
             if (r != 1) continue;
             total += s.Wq;
             dr++;
-            orc_splat_one(&P, &s, c->width, c->height, acc);
+            orc_splat_one(&P, &s, c->width, c->height, acc, NULL);
         }
     }
     if (total >> 64) st = ORC_ERR_RANGE;

@@ -100,6 +100,8 @@ def lib():
         L.orc_project.restype = C.c_int
         L.orc_splat_points.argtypes = [f32p, f32p, C.c_uint64, P(Camera), P(RParams), u64p, P(C.c_uint64)]
         L.orc_splat_points.restype = C.c_int
+        L.orc_count_updates.argtypes = [f32p, f32p, C.c_uint64, P(Camera), P(RParams)]
+        L.orc_count_updates.restype = C.c_uint64
         L.orc_splat_particles.argtypes = [f32p, f32p, f32p, C.c_uint64, P(Camera), P(RParams), u64p,
                                           P(C.c_uint64)]
         L.orc_splat_particles.restype = C.c_int
@@ -334,6 +336,13 @@ def splat_points(pts4, hs, cam: dict, rp: RParams):
     st = lib().orc_splat_points(pts4, np.ascontiguousarray(hs, np.float32), pts4.shape[0], C.byref(camera(cam)),
                                 C.byref(rp), acc, C.byref(nd))
     return acc.reshape(cam["height"], cam["width"]), st, int(nd.value)
+
+
+def count_updates(pts4, hs, cam: dict, rp: RParams) -> int:
+    """Pixel updates of drawing the points: (splat, pixel) pairs with a table index below 1024."""
+    pts4 = np.ascontiguousarray(pts4, np.float32).reshape(-1, 4)
+    return int(lib().orc_count_updates(pts4, np.ascontiguousarray(hs, np.float32), pts4.shape[0],
+                                       C.byref(camera(cam)), C.byref(rp)))
 
 
 def pixel_value(pts4, hs, cam: dict, rp: RParams, px: int, py: int) -> int:

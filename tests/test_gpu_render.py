@@ -124,6 +124,13 @@ def test_counting_pixel_updates_keeps_the_image(G, R):
     # the same frame counted by the tile shape that evaluates other pixel blocks gives the same count
     _, c = R.render(t, cam, G.make_params(count_updates=True, tile_w=16, tile_h=16))
     assert torch.equal(a, c) and R.stats()["pixel_updates"] == n
+    # and the count is the oracle's for the points of the nodes it selects
+    ot = O.build_tree(p.xyz, p.mass, p.h, seed=2, n_max=300)
+    rp = O.rparams(lambda_px=G.default_lambda(300))
+    sel = O.select(ot, cam, rp)
+    idx = np.concatenate([np.arange(int(ot.nodes[i]["point_first"]), int(ot.nodes[i]["point_first"])
+                                    + int(ot.nodes[i]["point_count"])) for i in sel])
+    assert n == O.count_updates(ot.pts4[idx], ot.hs[idx], cam, rp)
 
 
 @pytest.mark.parametrize("parts", [3, 17, 150])

@@ -246,3 +246,31 @@ def test_tonemap_closed_forms():
     ramp = np.sort(np.random.default_rng(0).integers(0, 2**50, 1000).astype(np.uint64))
     r = O.tonemap(ramp, O.rparams(tone_auto=1)).astype(int)
     assert np.all(np.diff(r) >= 0)
+
+
+def test_pixel_update_count():
+    """The counter of (splat, pixel) pairs inside the support, pinned by exact integer enumeration of
+    q S < 2^47 over a window around one splat (independent of the oracle's box logic), additivity
+    and the area of the 3-sigma disc."""
+    cam = _axis_camera(W=256, H=256, f=200.0)
+    rp = O.rparams()
+    pts = np.array([[0.5, 0.5, 0.5, 1.0]], np.float32)
+    for h in (0.002, 0.01, 0.03):
+        hs = np.array([h], np.float32)
+        n = O.count_updates(pts, hs, cam, rp)
+        ok, U, V, S, Wq = (int(v) for v in O.project(cam, rp, 0.5, 0.5, 0.5, 1.0, h))
+        assert ok == 1
+        brute = 0
+        for py in range(256):
+            dy = py * 256 + 128 - V
+            for px in range(256):
+                dx = px * 256 + 128 - U
+                if (dx * dx + dy * dy) * S < (1 << 47):
+                    brute += 1
+        assert n == brute
+        sigma = 200.0 * h / 1.5
+        if 3 * sigma < 100:
+            assert abs(n - math.pi * (3 * sigma) ** 2) < 0.1 * math.pi * (3 * sigma) ** 2 + 20
+    a = np.array([[0.5, 0.5, 0.5, 1.0], [0.45, 0.52, 0.5, 2.0], [0.6, 0.4, 0.55, 0.5]], np.float32)
+    ha = np.array([0.01, 0.004, 0.02], np.float32)
+    assert O.count_updates(a, ha, cam, rp) == sum(O.count_updates(a[i:i + 1], ha[i:i + 1], cam, rp) for i in range(3))
