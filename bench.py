@@ -50,6 +50,8 @@ def args_():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-brute", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-views", type=int, default=16, help="views per batch in the batched measurement")
+    ap.add_argument("--batch-capacity-log2", type=int, default=29, help="log2 of the batch record capacity")
     return ap.parse_args()
 
 
@@ -327,8 +329,9 @@ def run_ours(a):
     # batched views (one set of launches, no host waits) and its CUDA-graph replay
     batched = None
     if not a.no_batch:
-        bcams = cams[:: max(1, nf // 16)][:16]
-        cap = 1 << 29  # 8 GiB of (tile, splat) records for 16 views
+        nbv = max(1, a.batch_views)
+        bcams = cams[:: max(1, nf // nbv)][:nbv]
+        cap = 1 << a.batch_capacity_log2  # (tile, splat) records, 16 B each (2^29: 8 GiB for 16 views)
         tree = gblod.build_lod(xyz, mass, h, n_max=n_max, seed=1)
         bviews = [(tree, c, torch.empty((H, W), dtype=torch.uint8, device=dev),
                    torch.empty((H, W), dtype=torch.int64, device=dev)) for c in bcams]
