@@ -503,7 +503,7 @@ __device__ __forceinline__ void scatter_pairs(uint32_t n, uint32_t t00, int tw, 
 }
 
 template <class Src>
-__global__ void __launch_bounds__(RT) k_project_count(Src src, Proj P, unsigned long long e_lo,
+__global__ void __launch_bounds__(RT, 4) k_project_count(Src src, Proj P, unsigned long long e_lo,
                                                       unsigned long long e_hi, uint32_t *__restrict__ tile_cnt,
                                                       unsigned *status, FrameStatsDev *stats)
 {

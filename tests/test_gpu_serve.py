@@ -72,3 +72,40 @@ def test_overflowing_batches_fall_back_to_exact_views(setup):
     assert loop.stats["overflow_batches"] >= 1 and loop.stats["unserved"] == 0
     _check_alone(gblod, trees, loop, done)
     loop.close()
+
+
+def test_full_size_timestep_batch_equals_views_alone():
+    """One 75M-particle timestep of the serving workload at full size: a mixed-resolution batch of
+    session views (720p, 1080p, 4K) renders every view exactly as it renders alone."""
+    from paper_0811_2055_gb300 import gblod, serve
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    base = synth.timesteps_recipe()
+    x0, vel = torch.from_numpy(base.xyz).to(dev), torch.from_numpy(base.vel).to(dev)
+    mass, h = torch.from_numpy(base.mass).to(dev), torch.from_numpy(base.h).to(dev)
+    del base
+    xt = torch.remainder(x0 + 3 * vel, 1.0).contiguous()
+    del x0, vel
+    tree = gblod.build_lod(xt, mass, h, n_max=16000, seed=1)
+    del xt, mass, h
+    par = gblod.make_params()
+    cams = [serve.session_camera(s, 1.5 * s, w, hh) for s, (w, hh) in
+            enumerate([(1280, 720), (1920, 1080), (3840, 2160), (1920, 1080)])]
+    single = gblod.Renderer()
+    alone = []
+    for cam in cams:
+        img, acc = single.render(tree, cam, par)
+        alone.append((img.cpu().numpy(), gblod.u64(acc).copy()))
+    assert single.status() == gblod.OK
+    views = [(tree, cam, torch.empty((cam["height"], cam["width"]), dtype=torch.uint8, device=dev),
+              torch.empty((cam["height"], cam["width"]), dtype=torch.int64, device=dev)) for cam in cams]
+    rb = gblod.Renderer()
+    rb.reserve_batch(views, par, record_capacity=1 << 29)
+    rb.render_batch(views, par)
+    assert rb.status() == gblod.OK
+    for (_, _, img, acc), (ai, aa) in zip(views, alone):
+        assert np.array_equal(gblod.u64(acc), aa)
+        assert np.array_equal(img.cpu().numpy(), ai)
+    single.close()
+    rb.close()
+    tree.free()
