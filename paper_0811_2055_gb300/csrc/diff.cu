@@ -31,6 +31,7 @@ struct DRec {
     uint32_t idx;
     float u, v, s;
 };
+__device__ __forceinline__ DRec make_drec() { return DRec{0u, 0.f, 0.f, 1.f}; }
 
 struct DProj {
     float u, v, s, xc, yc, zc;
@@ -181,10 +182,58 @@ __global__ void __launch_bounds__(DRT) k_dforward(const DCam *__restrict__ cams,
         atomicAdd(&images[((size_t)(v0 + vl) * c.H + py) * c.W + px], acc);
 }
 
-// Adjoint, record-parallel: the tile's dL/dI values are staged in shared memory and each thread
-// takes whole records, walks the pixels of the tile inside the record's 3-sigma box and keeps the
-// record's partial derivatives in registers, so nothing is reduced across threads; every per-pixel
-// term is recomputed from (u, v, sigma).
+// The partial derivatives of one record over the pixels (x, y) = (x0 + i % bw, y0 + i / bw) of its box
+// for i = first, first + step, ...: the per-pixel terms are recomputed from (u, v, sigma).
+__device__ __forceinline__ void dgrad_pixels(const DRec &r, float wi, float (*sg)[DT + 1], int X0, int Y0, int x0,
+                                             int y0, int bw, int area, int first, int step, float &tw, float &tu,
+                                             float &tv, float &ts)
+{
+    const float s = r.s, s2 = s * s;
+    const float inv2s2 = 1.0f / (2.0f * s2), norm = INV_2PI_C / s2, e45 = E45 * (INV_2PI_C / s2);
+    for (int i = first; i < area; i += step) {
+        const int y = y0 + i / bw, x = x0 + i % bw;
+        const float g = sg[y][x];
+        const float dx = (float)(X0 + x) + 0.5f - r.u;
+        const float dy = (float)(Y0 + y) + 0.5f - r.v;
+        const float r2 = dx * dx + dy * dy;
+        if (g != 0.0f && r2 < 9.0f * s2) {
+            const float e = expf(-r2 * inv2s2) * norm;
+            const float k = e - e45;
+            const float gwv = g * wi;
+            tw += g * k;
+            tu += gwv * e * dx / s2;
+            tv += gwv * e * dy / s2;
+            ts += gwv * (e * r2 / (s2 * s) - 2.0f * k / s);
+        }
+    }
+}
+
+// chains a record's (w, u, v, sigma) derivatives to its position, weight and log smoothing length
+__device__ __forceinline__ void dgrad_commit(const DCam &c, const float *xyz, const float *logh, uint32_t idx,
+                                             float tw, float tu, float tv, float ts, float *gxyz, float *gw,
+                                             float *glogh)
+{
+    if (tw == 0.f && tu == 0.f && tv == 0.f && ts == 0.f) return;
+    DProj o;
+    dproject(c, xyz, logh, idx, o);
+    const float iz = 1.0f / o.zc;
+    const float dxc = tu * c.F * iz;
+    const float dyc = -tv * c.F * iz;
+    const float ds_dz = o.clamped ? 0.0f : -o.s * iz;
+    const float dzc = tu * (-c.F * o.xc * iz * iz) + tv * (c.F * o.yc * iz * iz) + ts * ds_dz;
+    atomicAdd(&gxyz[3 * idx], c.rx * dxc + c.ux * dyc + c.fx * dzc);
+    atomicAdd(&gxyz[3 * idx + 1], c.ry * dxc + c.uy * dyc + c.fy * dzc);
+    atomicAdd(&gxyz[3 * idx + 2], c.rz * dxc + c.uz * dyc + c.fz * dzc);
+    atomicAdd(&gw[idx], tw);
+    if (!o.clamped) atomicAdd(&glogh[idx], ts * o.s);
+}
+
+// Adjoint: the tile's dL/dI values are staged in shared memory.  Each lane takes one record; a
+// record whose box inside the tile is small is walked by its own lane with the partial derivatives
+// in registers, a large one is walked by the whole warp (lanes over its pixels) and reduced with
+// shuffles, so no lane is held up by a large record while the others idle.  Every per-pixel term is
+// recomputed from (u, v, sigma); nothing per pixel is stored.
+constexpr int DBIG = 64; // box pixels from which a record is walked by the warp
 __global__ void __launch_bounds__(DRT) k_dbackward(const DCam *__restrict__ cams, int v0, const DRec *__restrict__ rec,
                                                    const uint4 *__restrict__ items, const float *__restrict__ xyz,
                                                    const float *__restrict__ w, const float *__restrict__ logh,
@@ -192,6 +241,7 @@ __global__ void __launch_bounds__(DRT) k_dbackward(const DCam *__restrict__ cams
                                                    float *glogh)
 {
     __shared__ float sg[DT][DT + 1];
+    const int lane = threadIdx.x & 31;
     const uint4 it = items[blockIdx.x];
     const DCam &c0 = cams[v0];
     const uint32_t ntiles = (uint32_t)(c0.tiles_x * c0.tiles_y);
@@ -205,45 +255,51 @@ __global__ void __launch_bounds__(DRT) k_dbackward(const DCam *__restrict__ cams
     }
     __syncthreads();
     const int xw = min(DT, c.W - X0), yh = min(DT, c.H - Y0); // tile clipped to the image
-    for (uint32_t b = it.y + threadIdx.x; b < it.z; b += DRT) {
-        const DRec r = rec[b];
-        const float s = r.s, s2 = s * s;
-        const float R = 3.0f * s;
-        const int x0 = max(0, (int)floorf(r.u - R - 0.5f) - X0), x1 = min(xw - 1, (int)ceilf(r.u + R - 0.5f) - X0);
-        const int y0 = max(0, (int)floorf(r.v - R - 0.5f) - Y0), y1 = min(yh - 1, (int)ceilf(r.v + R - 0.5f) - Y0);
-        const float wi = w[r.idx];
-        const float inv2s2 = 1.0f / (2.0f * s2), norm = INV_2PI_C / s2, e45 = E45 * (INV_2PI_C / s2);
-        float tw = 0.f, tu = 0.f, tv = 0.f, ts = 0.f;
-        for (int y = y0; y <= y1; ++y) {
-            const float dy = (float)(Y0 + y) + 0.5f - r.v;
-            for (int x = x0; x <= x1; ++x) {
-                const float g = sg[y][x];
-                const float dx = (float)(X0 + x) + 0.5f - r.u;
-                const float r2 = dx * dx + dy * dy;
-                if (g != 0.0f && r2 < 9.0f * s2) {
-                    const float e = expf(-r2 * inv2s2) * norm;
-                    const float k = e - e45;
-                    const float gwv = g * wi;
-                    tw += g * k;
-                    tu += gwv * e * dx / s2;
-                    tv += gwv * e * dy / s2;
-                    ts += gwv * (e * r2 / (s2 * s) - 2.0f * k / s);
-                }
-            }
+    for (uint32_t b0 = it.y + (threadIdx.x & ~31u); b0 < it.z; b0 += DRT) {
+        const uint32_t b = b0 + lane;
+        DRec r = make_drec();
+        int x0 = 0, y0 = 0, bw = 0, area = 0;
+        float wi = 0.0f;
+        if (b < it.z) {
+            r = rec[b];
+            const float R = 3.0f * r.s;
+            x0 = max(0, (int)floorf(r.u - R - 0.5f) - X0);
+            const int x1 = min(xw - 1, (int)ceilf(r.u + R - 0.5f) - X0);
+            y0 = max(0, (int)floorf(r.v - R - 0.5f) - Y0);
+            const int y1 = min(yh - 1, (int)ceilf(r.v + R - 0.5f) - Y0);
+            bw = max(0, x1 - x0 + 1);
+            area = bw * max(0, y1 - y0 + 1);
+            wi = w[r.idx];
         }
-        if (tw != 0.f || tu != 0.f || tv != 0.f || ts != 0.f) {
-            DProj o;
-            dproject(c, xyz, logh, r.idx, o);
-            const float iz = 1.0f / o.zc;
-            const float dxc = tu * c.F * iz;
-            const float dyc = -tv * c.F * iz;
-            const float ds_dz = o.clamped ? 0.0f : -o.s * iz;
-            const float dzc = tu * (-c.F * o.xc * iz * iz) + tv * (c.F * o.yc * iz * iz) + ts * ds_dz;
-            atomicAdd(&gxyz[3 * r.idx], c.rx * dxc + c.ux * dyc + c.fx * dzc);
-            atomicAdd(&gxyz[3 * r.idx + 1], c.ry * dxc + c.uy * dyc + c.fy * dzc);
-            atomicAdd(&gxyz[3 * r.idx + 2], c.rz * dxc + c.uz * dyc + c.fz * dzc);
-            atomicAdd(&gw[r.idx], tw);
-            if (!o.clamped) atomicAdd(&glogh[r.idx], ts * o.s);
+        const bool big = area >= DBIG;
+        // small records: one lane each
+        if (!big && area > 0) {
+            float tw = 0.f, tu = 0.f, tv = 0.f, ts = 0.f;
+            dgrad_pixels(r, wi, sg, X0, Y0, x0, y0, bw, area, 0, 1, tw, tu, tv, ts);
+            dgrad_commit(c, xyz, logh, r.idx, tw, tu, tv, ts, gxyz, gw, glogh);
+        }
+        // large records: the whole warp, one after another
+        uint32_t m = __ballot_sync(0xffffffffu, big);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            DRec q;
+            q.idx = __shfl_sync(0xffffffffu, r.idx, src);
+            q.u = __shfl_sync(0xffffffffu, r.u, src);
+            q.v = __shfl_sync(0xffffffffu, r.v, src);
+            q.s = __shfl_sync(0xffffffffu, r.s, src);
+            const float qw = __shfl_sync(0xffffffffu, wi, src);
+            const int qx0 = __shfl_sync(0xffffffffu, x0, src), qy0 = __shfl_sync(0xffffffffu, y0, src);
+            const int qbw = __shfl_sync(0xffffffffu, bw, src), qarea = __shfl_sync(0xffffffffu, area, src);
+            float tw = 0.f, tu = 0.f, tv = 0.f, ts = 0.f;
+            dgrad_pixels(q, qw, sg, X0, Y0, qx0, qy0, qbw, qarea, lane, 32, tw, tu, tv, ts);
+            for (int d = 16; d > 0; d >>= 1) {
+                tw += __shfl_xor_sync(0xffffffffu, tw, d);
+                tu += __shfl_xor_sync(0xffffffffu, tu, d);
+                tv += __shfl_xor_sync(0xffffffffu, tv, d);
+                ts += __shfl_xor_sync(0xffffffffu, ts, d);
+            }
+            if (lane == 0) dgrad_commit(c, xyz, logh, q.idx, tw, tu, tv, ts, gxyz, gw, glogh);
         }
     }
 }
