@@ -161,6 +161,58 @@ __device__ __forceinline__ void splat_box(int U, int V, uint32_t S, int W, int H
     y1 = min(y1, H - 1);
 }
 
+// Points whose pixel box is at most DIRECT_BOX pixels on a side are not binned: the scatter pass
+// adds their contributions straight to the image, one 64-bit atomic per pixel inside the support.
+// The image is a sum of integers, so it is the same whichever pass adds a contribution and in
+// whatever order.  Small boxes are most of the drawn points (sigma clamped at its minimum) but a
+// small share of the pixel work, and each of their (tile, point) records would cost the splat
+// kernel a staging slot, a list entry and a block test for a few pixels.
+constexpr int DIRECT_BOX = 4;
+
+__device__ __forceinline__ bool direct_box(int x0, int x1, int y0, int y1)
+{
+    return x1 - x0 < DIRECT_BOX && y1 - y0 < DIRECT_BOX;
+}
+
+// The per-pixel rule for one point over its (clipped) pixel box: q = dx^2 + dy^2 from the pixel
+// centre, index (q S) >> 37, drawn iff the index is below 1024, contribution floor(Wq K / 2^16)
+// (= Wh K + floor(Wl K / 2^16)).  Every pixel of the box lies within the support's bounding radius,
+// so q S < 2^49.  Returns the pixel updates.
+__device__ __forceinline__ unsigned splat_direct(const Splat &s, int x0, int x1, int y0, int y1,
+                                                 const int32_t *__restrict__ K, unsigned long long *img, int W)
+{
+    const unsigned long long Wq = __float2ull_rn(s.Wf);
+    const unsigned long long Wh = Wq >> 16;
+    const uint32_t Wl = (uint32_t)(Wq & 0xFFFFull);
+    unsigned hits = 0;
+    for (int y = y0; y <= y1; ++y) {
+        const long long dy = (long long)y * 256 + 128 - s.V;
+        for (int x = x0; x <= x1; ++x) {
+            const long long dx = (long long)x * 256 + 128 - s.U;
+            const unsigned long long q = (unsigned long long)(dx * dx + dy * dy);
+            const unsigned long long idx = (q * (unsigned long long)s.S) >> 37;
+            if (idx < 1024ull) {
+                const uint32_t kv = (uint32_t)__ldg(&K[idx]);
+                const unsigned long long c = Wh * kv + ((Wl * kv) >> 16);
+                if (c) atomicAdd(&img[(size_t)y * W + x], c);
+                ++hits;
+            }
+        }
+    }
+    return hits;
+}
+
+// Adds a warp's pixel updates to the frame counters (every lane of the warp calls it)
+__device__ __forceinline__ void count_hits(unsigned hits, FrameStatsDev *stats)
+{
+    unsigned long long h64 = hits;
+    for (int d = 16; d > 0; d >>= 1) h64 += __shfl_xor_sync(0xffffffffu, h64, d);
+    if ((threadIdx.x & 31) == 0 && h64) {
+        atomicAdd(&stats->pixel_updates, h64);
+        atomicAdd(&stats->pixel_updates_total, h64);
+    }
+}
+
 // ------------------------------------------------------------------ R1
 struct Frustum {
     double n[5][3];
@@ -531,7 +583,7 @@ __global__ void __launch_bounds__(RT, 4) k_project_count(Src src, Proj P, unsign
                 ++splats;
                 int x0, x1, y0, y1;
                 splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
-                if (x0 <= x1 && y0 <= y1) {
+                if (x0 <= x1 && y0 <= y1 && !direct_box(x0, x1, y0, y1)) {
                     const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
                     pairs += (unsigned long long)(tx1 - tx0 + 1) * (unsigned long long)(ty1 - ty0 + 1);
                     for (int ty = ty0; ty <= ty1; ++ty)
@@ -555,12 +607,17 @@ __global__ void __launch_bounds__(RT, 4) k_project_count(Src src, Proj P, unsign
     amp.flush(stats);
 }
 
+// Writes the (tile, point) records of the binned points and splats the points with small boxes
+// into img; cstats (null: not counted) receives the pixel updates of the latter.
 template <class Src>
-__global__ void __launch_bounds__(RT) k_project_scatter(Src src, Proj P, unsigned long long e_lo,
-                                                        unsigned long long e_hi, uint32_t *__restrict__ cursor,
-                                                        uint4 *__restrict__ rec)
+__global__ void __launch_bounds__(RT, 4) k_project_scatter(Src src, Proj P, unsigned long long e_lo,
+                                                           unsigned long long e_hi, uint32_t *__restrict__ cursor,
+                                                           uint4 *__restrict__ rec, unsigned long long *img,
+                                                           FrameStatsDev *cstats)
 {
     const unsigned long long total = min(src_total(src), e_hi);
+    const int32_t *K = g_ktab[P.kernel];
+    unsigned hits = 0;
     for (unsigned long long a = e_lo + (unsigned long long)blockIdx.x * CHUNK; a < total;
          a += (unsigned long long)gridDim.x * CHUNK) {
         const unsigned long long b = min(total, a + CHUNK);
@@ -582,16 +639,21 @@ __global__ void __launch_bounds__(RT) k_project_scatter(Src src, Proj P, unsigne
                 int x0, x1, y0, y1;
                 splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
                 if (x0 <= x1 && y0 <= y1) {
-                    r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
-                    const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
-                    tw = tx1 - tx0 + 1;
-                    n = (uint32_t)(tw * (ty1 - ty0 + 1));
-                    t00 = (uint32_t)(ty0 * P.tiles_x + tx0);
+                    if (direct_box(x0, x1, y0, y1)) {
+                        hits += splat_direct(s, x0, x1, y0, y1, K, img, P.W);
+                    } else {
+                        r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
+                        const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
+                        tw = tx1 - tx0 + 1;
+                        n = (uint32_t)(tw * (ty1 - ty0 + 1));
+                        t00 = (uint32_t)(ty0 * P.tiles_x + tx0);
+                    }
                 }
             }
             scatter_pairs(n, t00, tw, P.tiles_x, r, cursor, rec, ~0ull);
         }
     }
+    if (cstats) count_hits(hits, cstats);
 }
 
 __global__ void k_tile_items(uint32_t ntiles, const uint32_t *tile_cnt, uint32_t *item_cnt)
@@ -852,16 +914,6 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
     }
 }
 
-__device__ __forceinline__ void count_hits(unsigned hits, FrameStatsDev *stats)
-{
-    unsigned long long h64 = hits;
-    for (int d = 16; d > 0; d >>= 1) h64 += __shfl_xor_sync(0xffffffffu, h64, d);
-    if ((threadIdx.x & 31) == 0 && h64) {
-        atomicAdd(&stats->pixel_updates, h64);
-        atomicAdd(&stats->pixel_updates_total, h64);
-    }
-}
-
 template <bool COUNT>
 __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
                                                        Proj P, unsigned long long *__restrict__ img,
@@ -986,7 +1038,7 @@ void bin_splat(gblod_renderer *r, const Src &src, const Proj &P, unsigned long l
     r->items.ensure(A, pc.items, s);
     GB_CUDA(cudaMemcpyAsync(r->tile_cur.p, r->tile_off.p, (size_t)ntiles * 4, cudaMemcpyDeviceToDevice, s));
     launch(GBLOD_K_PROJECT_SCATTER, k_project_scatter<Src>, dim3((unsigned)persistent_blocks(4)), dim3(RT), 0, s, src,
-           P, lo, hi, r->tile_cur.p, r->records.p);
+           P, lo, hi, r->tile_cur.p, r->records.p, img, r->count_updates ? r->stats : (FrameStatsDev *)nullptr);
     launch(GBLOD_K_RENDER_OTHER, k_fill_items, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
            (const uint32_t *)r->tile_cnt.p, (const uint32_t *)r->tile_off.p, (const uint32_t *)r->item_off.p,
            r->items.p);
@@ -1240,12 +1292,17 @@ __device__ __forceinline__ int bsrc_load(const SrcBatch &s, unsigned long long e
     return v;
 }
 
+// Counting pass (SCATTER false) or record pass (true) over the flat point space of a batch; the
+// record pass also splats the points with small boxes into their view's image, and counts their
+// pixel updates when count_updates is set.
 template <bool SCATTER>
 __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restrict__ tile_cnt,
                                                  uint32_t *__restrict__ cursor, uint4 *__restrict__ rec,
-                                                 unsigned long long rec_cap, unsigned *status, FrameStatsDev *stats)
+                                                 unsigned long long rec_cap, unsigned *status, FrameStatsDev *stats,
+                                                 int count_updates)
 {
     const unsigned long long total = *src.total;
+    unsigned hits = 0;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = gbd::lanemask_lt();
     unsigned long long splats = 0, pairs = 0;
@@ -1288,13 +1345,17 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
                 int x0, x1, y0, y1;
                 splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
                 if (x0 <= x1 && y0 <= y1) {
-                    const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
-                    tw = tx1 - tx0 + 1;
-                    n = (uint32_t)(tw * (ty1 - ty0 + 1));
-                    t00 = tb + (uint32_t)(ty0 * P.tiles_x + tx0);
-                    tiles_x = P.tiles_x;
-                    if (!SCATTER) pairs += n;
-                    r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
+                    if (direct_box(x0, x1, y0, y1)) {
+                        if (SCATTER) hits += splat_direct(s, x0, x1, y0, y1, g_ktab[P.kernel], src.views[v].accum, P.W);
+                    } else {
+                        const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
+                        tw = tx1 - tx0 + 1;
+                        n = (uint32_t)(tw * (ty1 - ty0 + 1));
+                        t00 = tb + (uint32_t)(ty0 * P.tiles_x + tx0);
+                        tiles_x = P.tiles_x;
+                        if (!SCATTER) pairs += n;
+                        r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
+                    }
                 }
             }
             if (SCATTER) {
@@ -1320,6 +1381,8 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
         if (lane == 0 && splats) atomicAdd(&stats->splats, splats);
         if (lane == 0 && pairs) atomicAdd(&stats->pairs, pairs);
         amp.flush(stats);
+    } else if (count_updates) {
+        count_hits(hits, stats);
     }
 }
 
@@ -1560,14 +1623,15 @@ void render_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod
     // R2: count, offsets, scatter
     const SrcBatch src{dv, r->b_sel.p, r->b_pfx.p, r->b_base.p, nsel, &r->stats->points};
     launch(GBLOD_K_PROJECT_COUNT, k_bproject<false>, dim3(G), dim3(RT), 0, s, src, r->tile_cnt.p,
-           (uint32_t *)nullptr, (uint4 *)nullptr, 0ull, r->status, r->stats);
+           (uint32_t *)nullptr, (uint4 *)nullptr, 0ull, r->status, r->stats, 0);
     scan_exclusive_u32(A, r->scan, r->tile_cnt.p, r->tile_off.p, b.ntiles, r->tile_off.p + b.ntiles, s);
     launch(GBLOD_K_RENDER_OTHER, k_tile_items, dim3((b.ntiles + 255) / 256), dim3(256), 0, s, b.ntiles,
            (const uint32_t *)r->tile_cnt.p, r->item_cnt.p);
     scan_exclusive_u32(A, r->scan, r->item_cnt.p, r->item_off.p, b.ntiles, r->item_off.p + b.ntiles, s);
     GB_CUDA(cudaMemcpyAsync(r->tile_cur.p, r->tile_off.p, (size_t)b.ntiles * 4, cudaMemcpyDeviceToDevice, s));
     launch(GBLOD_K_PROJECT_SCATTER, k_bproject<true>, dim3(G), dim3(RT), 0, s, src, (uint32_t *)nullptr,
-           r->tile_cur.p, r->records.p, (unsigned long long)r->b_rec_cap, r->status, r->stats);
+           r->tile_cur.p, r->records.p, (unsigned long long)r->b_rec_cap, r->status, r->stats,
+           (rp.flags & GBLOD_RENDER_COUNT_UPDATES) ? 1 : 0);
     launch(GBLOD_K_RENDER_OTHER, k_bfill_items, dim3((b.ntiles + 255) / 256), dim3(256), 0, s, b.ntiles,
            (const ViewDev *)dv, n, (const uint32_t *)r->tile_cnt.p, (const uint32_t *)r->tile_off.p,
            (const uint32_t *)r->item_off.p, r->items.p, (uint32_t)items_cap, (unsigned long long)r->b_rec_cap,
@@ -1831,14 +1895,15 @@ gblod_status render_brute_noalloc(const float *xyz, const float *mass, const flo
         fail(GBLOD_ERR_RANGE, "gblod_render_bruteforce_noalloc: the frame needs " + std::to_string(pairs64) +
                                   " (tile, splat) records, more than the fixed maximum of " +
                                   std::to_string(NA_RECORDS));
-    GB_CUDA(cudaMemcpyAsync(tile_cur, tile_off, ntiles * 4, cudaMemcpyDeviceToDevice, s));
-    launch(GBLOD_K_PROJECT_SCATTER, k_project_scatter<SrcFlat>, dim3(G), dim3(RT), 0, s, src, P, 0ull, ~0ull,
-           tile_cur, records);
-    launch(GBLOD_K_RENDER_OTHER, k_fill_items, dim3((nt + 255) / 256), dim3(256), 0, s, nt,
-           (const uint32_t *)tile_cnt, (const uint32_t *)tile_off, (const uint32_t *)item_off, items);
     const size_t npix = (size_t)P.W * P.H;
     unsigned long long *img = reinterpret_cast<unsigned long long *>(accum);
-    GB_CUDA(cudaMemsetAsync(img, 0, npix * 8, s));
+    GB_CUDA(cudaMemsetAsync(img, 0, npix * 8, s)); // before the scatter, which adds the small boxes
+    GB_CUDA(cudaMemcpyAsync(tile_cur, tile_off, ntiles * 4, cudaMemcpyDeviceToDevice, s));
+    launch(GBLOD_K_PROJECT_SCATTER, k_project_scatter<SrcFlat>, dim3(G), dim3(RT), 0, s, src, P, 0ull, ~0ull,
+           tile_cur, records, img,
+           (rp.flags & GBLOD_RENDER_COUNT_UPDATES) ? stats : (FrameStatsDev *)nullptr);
+    launch(GBLOD_K_RENDER_OTHER, k_fill_items, dim3((nt + 255) / 256), dim3(256), 0, s, nt,
+           (const uint32_t *)tile_cnt, (const uint32_t *)tile_off, (const uint32_t *)item_off, items);
     launch(GBLOD_K_SPLAT, (rp.flags & GBLOD_RENDER_COUNT_UPDATES) ? k_splat_tiles<true> : k_splat_tiles<false>,
            dim3(nitems), dim3(RT), 0, s, (const uint4 *)records, (const uint4 *)items, P, img, stats);
     if (image) {
