@@ -237,13 +237,13 @@ def run_ours(a):
 
     # census of one LOD pass and one brute pass (untimed; the counts are deterministic)
     tree = lod_step()
-    lod_counts = {"splats": 0, "points": 0, "pixel_updates": 0, "nodes": 0, "pairs": 0, "pairs_first": 0}
+    lod_counts = {"splats": 0, "points": 0, "pixel_updates": 0, "nodes": 0, "pairs": 0, "pairs_captured": 0}
     for k, cam in enumerate(cams):
         r.render(tree, cam, par_count, image=img, accum=acc)
         s = r.stats()
         lod_counts["pairs"] += s["pairs"]
-        if k == 0:
-            lod_counts["pairs_first"] = s["pairs"]
+        if a.workload == "mid" and k * 240 // nf == SPLAT_CAPTURE["path_frame"]:
+            lod_counts["pairs_captured"] = s["pairs"]
         lod_counts["splats"] += s["splats"]
         lod_counts["points"] += s["points"]
         lod_counts["pixel_updates"] += s["pixel_updates"]
@@ -459,9 +459,10 @@ def run_ours(a):
         "roofline": {"kernel": "k_splat_tiles (R3)", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak if peak else None,
                      "traffic": splat_traffic(a, lod_counts, nf),
-                     "traffic_note": "DRAM read + write bytes of one ncu capture of the splat kernel (first frame of the "
-                                     "mid fly-through), scaled to the mean launch by its (tile, splat) records; null "
-                                     "when the kernel source differs from the captured one or the workload is not mid",
+                     "traffic_note": "DRAM read + write bytes of one ncu capture of the splat kernel (frame "
+                                     f"{SPLAT_CAPTURE['path_frame']} of the 240-frame mid path), scaled to the mean "
+                                     "launch by its (tile, splat) records; null when the kernel source or binning rule "
+                                     "differs from the captured one or the workload is not mid",
                      "launches": int(splat_launches), "avg_launch_ms": splat_ms / max(splat_launches, 1),
                      "peak_note": "152 SMs x 128 lanes x 2070 MHz (no measured ALU peak in MEASURED_PEAKS.json)"},
     }
@@ -473,17 +474,21 @@ def run_ours(a):
 
 
 def splat_source(src: bytes) -> bytes:
-    """The splat kernel's source: render.cu from `struct SplatSmem` to the end of `k_splat_tiles`."""
+    """The text the splat kernel's traffic depends on: render.cu's rule for which points are binned
+    (from `constexpr int DIRECT_BOX` to the end of `direct_box`) followed by the kernel itself (from
+    `struct SplatSmem` to the end of `k_splat_tiles`)."""
+    r0 = src.index(b"constexpr int DIRECT_BOX")
+    r1 = src.index(b"\n}\n", src.index(b"bool direct_box(", r0)) + 3
     a = src.index(b"struct SplatSmem {")
     b = src.index(b"\n}\n", src.index(b"k_splat_tiles(", a)) + 3
-    return src[a:b]
+    return src[r0:r1] + src[a:b]
 
 
-# DRAM bytes of one ncu capture of the splat kernel (--set full, frame 0 of the 24-frame mid fly-through,
-# default tile) and the sha256 of the kernel source it was taken of (render.cu from `struct SplatSmem`
-# to the end of `k_splat_tiles`); the ncu summary under profiles/ lists the same numbers.
-SPLAT_CAPTURE = {"source_sha256": "1391e5171ec27911ab47cb53e64aafd6e349766571f2953a3f7252b8f02d1258",
-                 "dram_read_bytes": 469.156352e6, "dram_write_bytes": 16.673024e6}
+# DRAM bytes of one ncu capture of the splat kernel (--set full, default tile; the frame of the 240-frame
+# mid path given by path_frame, drawn by the census pass) and the sha256 of the source text above at the
+# time of the capture; the ncu summary under profiles/ lists the same numbers.
+SPLAT_CAPTURE = {"source_sha256": "84df3723180f4af9614404d5e02fe1e2dca24577cac86f10ade50dbcdcdf77e1",
+                 "path_frame": 160, "dram_read_bytes": 444.259840e6, "dram_write_bytes": 16.311552e6}
 
 
 def splat_traffic(a, lod_counts, nf):
@@ -497,10 +502,10 @@ def splat_traffic(a, lod_counts, nf):
         return None
     if hashlib.sha256(splat_source(src)).hexdigest() != SPLAT_CAPTURE["source_sha256"]:
         return None
-    if a.workload != "mid" or a.particles or not lod_counts["pairs_first"]:
+    if a.workload != "mid" or a.particles or not lod_counts["pairs_captured"]:
         return None
     captured = SPLAT_CAPTURE["dram_read_bytes"] + SPLAT_CAPTURE["dram_write_bytes"]
-    return captured * (lod_counts["pairs"] / nf) / lod_counts["pairs_first"]
+    return captured * (lod_counts["pairs"] / nf) / lod_counts["pairs_captured"]
 
 
 # ------------------------------------------------------------------ the oracle (CPU)
