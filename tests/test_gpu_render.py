@@ -236,3 +236,79 @@ def test_mid_workload_full_size_frames(G, R):
     _, acc = R.render_bruteforce(*d, cam, G.make_params())
     want, _, _ = O.splat_particles(p.xyz, p.mass, p.h, cam, O.rparams())
     assert np.array_equal(G.u64(acc), want)
+
+
+def _at_pixel(cam, u, v, d):
+    """World point at depth d along the view whose projection is pixel position (u, v)."""
+    e, r, up, f = (np.asarray(cam[k], np.float64) for k in ("eye", "right", "up", "fwd"))
+    return e + d * f + ((u - cam["cx"]) * d / cam["f_px"]) * r - ((v - cam["cy"]) * d / cam["f_px"]) * up
+
+
+def _box_sides(cam, rp, pts4, h):
+    """Coverage only: how many drawn points have a clipped pixel box of at most 8 x 8 pixels (the
+    library's rule, restated: support bound sqrt(2^47 / S) + 2 in 1/256 px around the centre)."""
+    small = binned = 0
+    for i in range(len(h)):
+        r = O.project(cam, rp, *pts4[i].tolist(), float(h[i]))
+        if r[0] != 1:
+            continue
+        U, V, S = r[1], r[2], r[3]
+        rr = int(np.sqrt(np.float32(2.0 ** 47) / np.float32(S))) + 2
+        x0, x1 = max(-((rr + 128 - U) >> 8), 0), min((U - 128 + rr) >> 8, cam["width"] - 1)
+        y0, y1 = max(-((rr + 128 - V) >> 8), 0), min((V - 128 + rr) >> 8, cam["height"] - 1)
+        if x0 > x1 or y0 > y1:
+            continue
+        if x1 - x0 < 8 and y1 - y0 < 8:
+            small += 1
+        else:
+            binned += 1
+    return small, binned
+
+
+def test_small_boxes_splatted_without_binning(G, R):
+    """Points whose pixel box is at most 8 x 8 skip the tile records and are added to the image by
+    the scatter pass: sigma from the 0.5 px clamp to 3 px (boxes on both sides of the rule), image
+    borders and corners, 400 coincident points (same-pixel atomics) and large splats centred off
+    screen that reach only a corner's few pixels.  Same image and pixel-update count as the oracle,
+    for two tile shapes, brute force and full-depth LOD."""
+    cam = synth.look_at((0.5, 0.5, -1.0), (0.5, 0.5, 0.5), width=96, height=64)
+    rng = np.random.default_rng(31)
+    d = 1.5
+    n = 6000
+    u = rng.uniform(-4.0, cam["width"] + 4.0, n)
+    v = rng.uniform(-4.0, cam["height"] + 4.0, n)
+    sigma = np.exp(rng.uniform(np.log(0.3), np.log(3.0), n))
+    xyz = np.array([_at_pixel(cam, a, b, d) for a, b in zip(u, v)])
+    h = sigma * d / cam["f_px"]
+    # coincident points on one pixel, all with the clamped sigma
+    xyz[:400] = _at_pixel(cam, 40.3, 21.7, d)
+    h[:400] = 1e-5
+    # large splats (sigma 6 px) whose support reaches only a few pixels of a corner
+    for i, (cu, cv) in enumerate([(-3.2, -2.9), (cam["width"] + 3.3, -3.1), (-2.8, cam["height"] + 3.4),
+                                  (cam["width"] + 3.1, cam["height"] + 2.7), (-4.0, 30.0)]):
+        xyz[400 + i] = _at_pixel(cam, cu, cv, d)
+        h[400 + i] = 2.0 * d / cam["f_px"]
+    xyz = xyz.astype(np.float32)
+    h = h.astype(np.float32)
+    mass = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    dv = to_dev(xyz, mass, h)
+    rp = O.rparams()
+    want, st, nd = O.splat_particles(xyz, mass, h, cam, rp)
+    assert st == 0 and nd > 5000
+    pts4 = np.concatenate([xyz, mass[:, None]], 1).astype(np.float32)
+    n_upd = O.count_updates(pts4, h, cam, rp)
+    small, binned = _box_sides(cam, rp, pts4, h)
+    assert small > 3000 and binned > 1500  # both sides of the rule are exercised
+    for tile in ((64, 16), (8, 8)):
+        _, acc = R.render_bruteforce(*dv, cam, G.make_params(tile_w=tile[0], tile_h=tile[1], count_updates=True))
+        assert R.status() == G.OK
+        assert np.array_equal(G.u64(acc), want), tile
+        s = R.stats()
+        assert s["splats"] == nd and s["pixel_updates"] == n_upd, tile
+    # full depth equals brute force while no depth-21 node is lossy: the 400 coincident points share
+    # one depth-21 cell, so n_max must exceed 400
+    t = G.build_lod(*dv, n_max=1000, seed=5)
+    assert not np.any(t.export()["nodes"]["flags"] & G.NODE_LOSSY)
+    _, a = R.render(t, cam, G.make_params(lambda_px=0.0, count_updates=True))
+    assert np.array_equal(G.u64(a), want) and R.stats()["pixel_updates"] == n_upd
+    t.free()
