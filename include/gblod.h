@@ -234,7 +234,8 @@ typedef struct {
     uint64_t nodes_selected; /* R1 output */
     uint64_t points;         /* points fed to R2 */
     uint64_t splats;         /* points drawn after culling */
-    uint64_t pairs;          /* (tile, splat) records */
+    uint64_t pairs;          /* (tile, splat) records; a point whose clipped pixel box is at most
+                                8 x 8 pixels is drawn without records (added to the image directly) */
     uint64_t tiles;
     uint64_t amplitude_lo, amplitude_hi; /* sum of drawn amplitudes */
     uint64_t pixel_updates;  /* (splat, pixel) pairs inside the kernel support (0 unless the frame

@@ -675,10 +675,10 @@ __global__ void k_fill_items(uint32_t ntiles, const uint32_t *tile_cnt, const ui
 
 // ------------------------------------------------------------------ R3
 // One block per work item (a tile and up to ITEM of its records).  The tile is cut into 8 x 4
-// pixel blocks, one lane per pixel; block b belongs to warp b % 8 (up to SPLAT_SLOTS blocks per
-// warp).  Records are staged through shared memory in batches of RT; each warp first compacts,
-// by ballot, the records whose box touches each of its blocks, then evaluates only those for its
-// pixels and keeps the sums in registers (no atomics).
+// pixel blocks, one lane per pixel; each warp owns up to SPLAT_SLOTS blocks of one block column
+// (see strip_height).  Records are staged through shared memory STAGE at a time and listed per
+// block column; each warp compacts, by ballot, its column's records whose support reaches one of
+// its blocks, evaluates only those for its pixels and keeps the sums in registers.
 // Exact integer shortcuts of the per-pixel rule, all identities:
 //   (q S) >> 37 < 1024  <=>  q < QL = floor((2^47 - 1) / S) + 1     (one compare per miss)
 //   floor(Wq K / 2^16)   =   Wh K + floor(Wl K / 2^16),  Wq = Wh 2^16 + Wl, Wl < 2^16
