@@ -15,8 +15,12 @@ the float path (not the exact integer path):
                dL/du = sum g w E (x+1/2-u)/s^2,  dL/dv = sum g w E (y+1/2-v)/s^2,
                dL/ds = sum g w (E r^2/s^3 - 2 K/s);  then u, v, s -> p, l by the chain rule.
 
-Pinned by central finite differences of `forward` in FP64 (tests/test_oracle_diff.py) and by
-the kernel's closed forms (unit integral, continuity at the support edge).
+Pinned by central finite differences of `forward` in FP64 (tests/test_oracle_diff.py), by the
+kernel's closed forms (unit integral, continuity at the support edge, mirror symmetry on axis),
+and, for the camera convention, by the integer oracle: one splat's centroid lies at the integer
+oracle's projected position (U/256, V/256) within 0.02 px for points off axis in +x, +y and both
+together, seen from an axis-aligned and an oblique camera, and both images agree as truncated
+Gaussians of the same sigma.
 """
 from __future__ import annotations
 

@@ -36,7 +36,10 @@
  *   orc_render_lod      full-depth render equals the brute-force render of every particle
  *                       (the paper's "indistinguishable from a full rendering" goal at its limit)
  *   orc_select          lambda = 0 gives every visible leaf, lambda = inf gives the root,
- *                       a camera inside a node refines it, depth falls with distance
+ *                       a camera inside a node refines it, depth falls with distance; the
+ *                       refine/emit boundary by eyes, lambdas and focal lengths a relative
+ *                       1e-9 to either side of hand-worked thresholds (root and child cells,
+ *                       on axis, off axis at an edge distance, inside z_near)
  *   orc_tonemap         closed forms on synthetic accumulators
  *   orc_block_quantize  hand-worked codes, the half-step error bound, lossless decode once the
  *                       step is below half an ulp, decode-encode round trips, bounds that

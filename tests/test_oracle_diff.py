@@ -77,3 +77,50 @@ def test_clamped_sigma_has_no_log_h_gradient():
     g = np.ones((cam["height"], cam["width"]))
     _, _, dl = D.backward(cam, p, np.array([1.0]), np.log([1e-6]), g)
     assert dl[0] == 0.0
+
+
+def _int_splat(cam, x, y, z, w, h):
+    from oracle import oracle as O
+    return O.splat_points(np.array([[x, y, z, w]], np.float32), np.array([h], np.float32), cam,
+                          O.rparams())[0].astype(np.float64) / 2**32
+
+
+@pytest.mark.parametrize("eye,target", [((0.5, 0.5, -1.0), (0.5, 0.5, 0.5)),
+                                        ((1.4, 0.9, -0.6), (0.45, 0.55, 0.5))])
+@pytest.mark.parametrize("off", [(0.08, 0.0, 0.0), (0.0, 0.06, 0.0), (0.07, 0.05, 0.0), (-0.05, -0.07, 0.04)])
+def test_camera_convention_matches_integer_oracle(eye, target, off):
+    # one splat: the float image's centroid must sit where the integer oracle projects the point
+    # (U/256, V/256), for points displaced along +x and +y (both signs of both image axes), and
+    # the two images must agree as truncated Gaussians of the same sigma
+    from oracle import oracle as O
+    cam = synth.look_at(eye, target, width=128, height=96)
+    cam["f_px"] = 120.0
+    p = np.array([target[0] + off[0], target[1] + off[1], target[2] + off[2]], np.float32)
+    h = np.float32(0.006)
+    drawn, U, V, _, _ = O.project(cam, O.rparams(), float(p[0]), float(p[1]), float(p[2]), 1.0, float(h))
+    assert drawn == 1
+    img = D.forward(cam, p[None].astype(np.float64), np.array([1.0]), np.log([float(h)]))
+    H, W = img.shape
+    py, px = np.mgrid[0:H, 0:W]
+    m = img.sum()
+    u = float((img * (px + 0.5)).sum() / m)
+    v = float((img * (py + 0.5)).sum() / m)
+    assert abs(u - U / 256.0) < 0.02 and abs(v - V / 256.0) < 0.02, (u, v, U / 256.0, V / 256.0)
+    # image orientation by definition: displaced along the camera's right vector -> right of
+    # the image centre; along its up vector -> above it (image y grows downwards)
+    d = p.astype(np.float64) - np.asarray(target, np.float64)
+    along_r, along_u = float(d @ np.asarray(cam["right"])), float(d @ np.asarray(cam["up"]))
+    if abs(along_r) > 1e-3:
+        assert (u > cam["cx"]) == (along_r > 0)
+    if abs(along_u) > 1e-3:
+        assert (v < cam["cy"]) == (along_u > 0)
+    ref = _int_splat(cam, float(p[0]), float(p[1]), float(p[2]), 1.0, float(h))
+    assert np.abs(img - ref).sum() < 0.1 * ref.sum()
+
+
+def test_float_splat_mirror_symmetric_on_axis():
+    cam = _cam(W=96, H=64, f=150.0)
+    img = D.forward(cam, np.array([[0.5, 0.5, 0.5]]), np.array([1.0]), np.log([0.05]))
+    assert img.sum() > 0
+    assert np.allclose(img, img[:, ::-1], rtol=0, atol=1e-15 * img.max())
+    assert np.allclose(img, img[::-1, :], rtol=0, atol=1e-15 * img.max())
