@@ -84,7 +84,7 @@ typedef struct {
     double lambda_px;   /* detail threshold in pixels */
     double sigma_min_px, sigma_max_px;
     double tone_lo, tone_hi; /* fixed tone range (intensity units) when tone_auto == 0 */
-    int32_t kernel;     /* 0 Gaussian (disc), 1 cubic spline, 2 Gaussian (box, separable) */
+    int32_t kernel;     /* 0 Gaussian, 1 cubic spline */
     int32_t tone_auto;
 } orc_rparams;
 
@@ -192,9 +192,7 @@ double orc_cbrt(double t)
  *   kernel 0: truncated Gaussian exp(-q/2), Qmax = 9 (support 3 sigma)
  *   kernel 1: M4 cubic spline (Monaghan 1992) with xi = r/h: 1 - 1.5 xi^2 + 0.75 xi^3 (xi < 1),
  *             0.25 (2 - xi)^3 (xi < 2), Qmax = 4 (support 2 h).  The paper's blob is a
- *             "radial cubic function"; the Gaussian is the default workload kernel.
- *   kernel 2: the same Gaussian table read once per image axis, q = d^2 / sigma^2 of that
- *             axis's offset d (a Gaussian is the product of its two 1D factors). */
+ *             "radial cubic function"; the Gaussian is the default workload kernel. */
 void orc_kernel_table(int kernel, int32_t *K)
 {
     double qmax = kernel == 1 ? 4.0 : 9.0;
@@ -224,8 +222,6 @@ static const float ORC_A_GAUSS = 0x1.499c68p+29f;
 static const float ORC_A_CUBIC = 0x1.d1a452p+30f;
 static const float ORC_B_GAUSS = 0x1.c71c72p+27f;
 static const float ORC_B_CUBIC = 0x1p+29f;
-/*   A_box = 2^32 / (2 pi erf(3/sqrt 2)^2)  (2D Gaussian, renormalised to its 3-sigma square) */
-static const float ORC_A_BOX = 0x1.47b76ap+29f;
 
 /* ------------------------------------------------------------------ Morton keys */
 /* Root cube [lo, lo + side)^3; per axis q = clamp(floor((x - lo) * 2^21 / side), 0, 2^21-1)
@@ -665,7 +661,6 @@ int orc_build_topdown(const float *xyz, const uint32_t *ids, uint64_t n, uint32_
 typedef struct {
     float ex, ey, ez, rx, ry, rz, ux, uy, uz, fx, fy, fz;
     float F, CX, CY, ZN, smin, smax, A, B, Rk, Wimg, Himg;
-    int32_t kernel;
     int32_t K[ORC_T];
 } orc_proj;
 
@@ -688,8 +683,7 @@ static void orc_proj_init(orc_proj *P, const orc_camera *c, const orc_rparams *r
     P->ZN = (float)c->z_near;
     P->smin = (float)rp->sigma_min_px;
     P->smax = (float)rp->sigma_max_px;
-    P->kernel = rp->kernel;
-    P->A = rp->kernel == 1 ? ORC_A_CUBIC : (rp->kernel == 2 ? ORC_A_BOX : ORC_A_GAUSS);
+    P->A = rp->kernel == 1 ? ORC_A_CUBIC : ORC_A_GAUSS;
     P->B = rp->kernel == 1 ? ORC_B_CUBIC : ORC_B_GAUSS;
     P->Rk = rp->kernel == 1 ? 2.0f : 3.0f;
     P->Wimg = (float)c->width;
@@ -750,35 +744,11 @@ int orc_project(const orc_camera *c, const orc_rparams *rp, float x, float y, fl
     return r;
 }
 
-/* The contribution of splat s to the pixel whose centre lies (ddx, ddy) from the splat centre
- * (1/256 px units).  Returns 1 and sets *c if the pixel is inside the support, else 0.
- *   kernels 0, 1 (radial): q = ddx^2 + ddy^2, i = (q S) >> 37; inside iff i < 1024;
- *                          c = floor(Wq K[i] / 2^16)
- *   kernel 2 (separable):  i = (ddx^2 S) >> 37, j = (ddy^2 S) >> 37; inside iff both < 1024;
- *                          c = floor(Wq K[j] K[i] / 2^32)
- * All products are exact (128-bit). */
-static int orc_pixel_rule(const orc_proj *P, const orc_splat *s, int64_t ddx, int64_t ddy, uint64_t *c)
-{
-    if (P->kernel == 2) {
-        u128 ix = ((u128)(uint64_t)(ddx * ddx) * (u128)s->S) >> 37;
-        u128 iy = ((u128)(uint64_t)(ddy * ddy) * (u128)s->S) >> 37;
-        if (ix >= ORC_T || iy >= ORC_T) return 0;
-        u128 p = (u128)s->Wq * (u128)(uint32_t)P->K[(int)iy] * (u128)(uint32_t)P->K[(int)ix];
-        *c = (uint64_t)(p >> 32);
-        return 1;
-    }
-    uint64_t q = (uint64_t)(ddx * ddx + ddy * ddy);
-    u128 idx = ((u128)q * (u128)s->S) >> 37;
-    if (idx >= ORC_T) return 0;
-    *c = (uint64_t)(((u128)s->Wq * (u128)(uint32_t)P->K[(int)idx]) >> 16);
-    return 1;
-}
-
-/* Adds one splat to acc (if acc != NULL): every pixel centre (256 px + 128, 256 py + 128) inside
- * the support gets the contribution of orc_pixel_rule; counts the pixel updates, the (splat,
- * pixel) pairs inside the support, into *updates (if updates != NULL).  The pixel loop covers a
- * generous box (the support reaches at most sqrt(2^47 / S) from the centre on either axis); the
- * table test decides. */
+/* Adds one splat into the W x H accumulator: every pixel centre (256 px + 128, 256 py + 128)
+ * gets floor(Wq K[i] / 2^16) where i = (q S) >> 37 and q is the squared distance in 1/256 px,
+ * provided i < 1024.  The pixel loop covers a generous box; the table test decides. */
+/* Adds one splat to acc (if acc != NULL) and counts its pixel updates, the (splat, pixel) pairs
+ * with a table index below 1024, into *updates (if updates != NULL). */
 static void orc_splat_one(const orc_proj *P, const orc_splat *s, int W, int H, uint64_t *acc, uint64_t *updates)
 {
     /* support radius in 1/256 px: q S < 1024 * 2^37 needs q < 2^47 / S */
@@ -794,9 +764,12 @@ static void orc_splat_one(const orc_proj *P, const orc_splat *s, int W, int H, u
         for (int64_t px = x0; px <= x1; ++px) {
             int64_t ddx = px * 256 + 128 - (int64_t)s->U;
             int64_t ddy = py * 256 + 128 - (int64_t)s->V;
-            uint64_t c = 0;
-            if (orc_pixel_rule(P, s, ddx, ddy, &c)) {
-                if (acc) acc[py * W + px] += c;
+            uint64_t q = (uint64_t)(ddx * ddx + ddy * ddy);
+            u128 qs = (u128)q * (u128)s->S;
+            u128 idx = qs >> 37;
+            if (idx < ORC_T) {
+                u128 c = ((u128)s->Wq * (u128)(uint32_t)P->K[(int)idx]) >> 16;
+                if (acc) acc[py * W + px] += (uint64_t)c;
                 if (updates) ++*updates;
             }
         }
@@ -880,8 +853,9 @@ uint64_t orc_pixel_value(const float *pts4, const float *hs, uint64_t n, const o
             continue;
         int64_t ddx = (int64_t)px * 256 + 128 - (int64_t)s.U;
         int64_t ddy = (int64_t)py * 256 + 128 - (int64_t)s.V;
-        uint64_t c = 0;
-        if (orc_pixel_rule(&P, &s, ddx, ddy, &c)) acc += c;
+        u128 qs = (u128)(uint64_t)(ddx * ddx + ddy * ddy) * (u128)s.S;
+        u128 idx = qs >> 37;
+        if (idx < ORC_T) acc += (uint64_t)(((u128)s.Wq * (u128)(uint32_t)P.K[(int)idx]) >> 16);
     }
     return acc;
 }
@@ -1236,11 +1210,10 @@ void orc_neglogs(const uint64_t *u, uint64_t n, double *out)
 }
 
 /* fp32 normalisation constants, for the tests: {A_gauss, A_cubic, B_gauss, B_cubic} */
-void orc_constants(float out[5])
+void orc_constants(float out[4])
 {
     out[0] = ORC_A_GAUSS;
     out[1] = ORC_A_CUBIC;
     out[2] = ORC_B_GAUSS;
     out[3] = ORC_B_CUBIC;
-    out[4] = ORC_A_BOX;
 }

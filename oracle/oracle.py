@@ -126,9 +126,9 @@ def lib():
 
 
 def constants():
-    out = np.zeros(5, np.float32)
+    out = np.zeros(4, np.float32)
     lib().orc_constants(out)
-    return dict(A_gauss=out[0], A_cubic=out[1], B_gauss=out[2], B_cubic=out[3], A_box=out[4])
+    return dict(A_gauss=out[0], A_cubic=out[1], B_gauss=out[2], B_cubic=out[3])
 
 
 # ------------------------------------------------------------------ small functions
