@@ -9,9 +9,11 @@
  * it is written as slow, direct loops so that it can be checked against the paper (and
  * against the readings of the paper listed beside each function) by eye.
  *
- * Build: gcc -O2 -std=gnu11 -ffp-contract=off -fPIC -shared oracle.c -lm
+ * Build: gcc -O2 -std=gnu11 -ffp-contract=off -fopenmp -fPIC -shared oracle.c -lm
  * (-ffp-contract=off: every float/double operation below rounds on its own; nothing is
- * fused into an FMA.)
+ * fused into an FMA.  -fopenmp only splits the points of a frame between threads, each with
+ * an image of its own, and the images are summed as integers: the result does not depend on
+ * the number of threads; without OpenMP everything runs on one thread.)
  *
  * Precision: FP64 for everything the method does not fix (node geometry, the detail
  * criterion, node masses, statistics); the per-point projection is specified in fp32
@@ -56,6 +58,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef unsigned __int128 u128;
 
@@ -776,30 +781,97 @@ static void orc_splat_one(const orc_proj *P, const orc_splat *s, int W, int H, u
     }
 }
 
+/* Threads used by the frame loops below (0: as many as OpenMP offers). */
+static int orc_threads = 0;
+void orc_set_threads(int n) { orc_threads = n < 0 ? 0 : n; }
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return orc_threads > 0 ? orc_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* A list of points to draw: point k is row idx[k] (or row k if idx is NULL) of either float4
+ * (x, y, z, weight) rows + h, or of the input layout (xyz rows, mass, h). */
+typedef struct {
+    const float *pts4, *hs;
+    const float *xyz, *mass, *h;
+    const uint64_t *idx;
+} orc_src;
+
+static void orc_src_get(const orc_src *S, uint64_t k, float *x, float *y, float *z, float *w, float *h)
+{
+    uint64_t j = S->idx ? S->idx[k] : k;
+    if (S->pts4) {
+        *x = S->pts4[4 * j]; *y = S->pts4[4 * j + 1]; *z = S->pts4[4 * j + 2]; *w = S->pts4[4 * j + 3];
+        *h = S->hs[j];
+    } else {
+        *x = S->xyz[3 * j]; *y = S->xyz[3 * j + 1]; *z = S->xyz[3 * j + 2]; *w = S->mass[j];
+        *h = S->h[j];
+    }
+}
+
+/* Draws the n points of S into acc (W x H, added to what it holds): R2 then the per-pixel rule
+ * of every drawn point.  The points are shared out between threads, each adding into an image of
+ * its own; the images are then summed as integers.  Returns ORC_OK, or ORC_ERR_RANGE if a drawn
+ * point's amplitude was out of range or the sum of drawn amplitudes reached 2^64 (a pixel could
+ * then wrap). */
+static int orc_splat_src(const orc_proj *P, const orc_src *S, uint64_t n, int W, int H, uint64_t *acc,
+                         uint64_t *n_drawn)
+{
+    int T = orc_get_threads();
+    if (T > 64) T = 64;
+    size_t npix = (size_t)W * (size_t)H;
+    uint64_t *img = (uint64_t *)calloc((size_t)T * npix, sizeof(uint64_t));
+    int bad[64] = {0};
+    u128 tot[64] = {0};
+    uint64_t dr[64] = {0};
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(T) schedule(dynamic, 4096)
+#endif
+    for (uint64_t k = 0; k < n; ++k) {
+#ifdef _OPENMP
+        int t = omp_get_thread_num();
+#else
+        int t = 0;
+#endif
+        float x, y, z, w, h;
+        orc_src_get(S, k, &x, &y, &z, &w, &h);
+        orc_splat s;
+        int r = orc_project_one(P, x, y, z, w, h, &s);
+        if (r < 0) bad[t] = 1;
+        if (r != 1) continue;
+        tot[t] += s.Wq;
+        dr[t]++;
+        orc_splat_one(P, &s, W, H, img + (size_t)t * npix, NULL);
+    }
+    int st = ORC_OK;
+    u128 total = 0;
+    uint64_t drawn = 0;
+    for (int t = 0; t < T; ++t) {
+        if (bad[t]) st = ORC_ERR_RANGE;
+        total += tot[t];
+        drawn += dr[t];
+    }
+    for (size_t i = 0; i < npix; ++i)
+        for (int t = 0; t < T; ++t) acc[i] += img[(size_t)t * npix + i];
+    free(img);
+    if (total >> 64) st = ORC_ERR_RANGE;
+    if (n_drawn) *n_drawn = drawn;
+    return st;
+}
+
 /* Brute-force render of a point list (x, y, z, weight as float4 rows + h): the plain
- * definition of the image.  acc must hold width*height zeros (or a partial image to add to).
- * Returns ORC_OK, or ORC_ERR_RANGE if a drawn point's amplitude was out of range or the sum
- * of drawn amplitudes reached 2^64 (a pixel could then wrap). */
+ * definition of the image.  acc must hold width*height zeros (or a partial image to add to). */
 int orc_splat_points(const float *pts4, const float *hs, uint64_t n, const orc_camera *c, const orc_rparams *rp,
                      uint64_t *acc, uint64_t *n_drawn)
 {
     orc_proj P;
     orc_proj_init(&P, c, rp);
-    int st = ORC_OK;
-    u128 total = 0;
-    uint64_t drawn = 0;
-    for (uint64_t i = 0; i < n; ++i) {
-        orc_splat s;
-        int r = orc_project_one(&P, pts4[4 * i], pts4[4 * i + 1], pts4[4 * i + 2], pts4[4 * i + 3], hs[i], &s);
-        if (r < 0) st = ORC_ERR_RANGE;
-        if (r != 1) continue;
-        total += s.Wq;
-        drawn++;
-        orc_splat_one(&P, &s, c->width, c->height, acc, NULL);
-    }
-    if (total >> 64) st = ORC_ERR_RANGE;
-    if (n_drawn) *n_drawn = drawn;
-    return st;
+    orc_src S = {pts4, hs, NULL, NULL, NULL, NULL};
+    return orc_splat_src(&P, &S, n, c->width, c->height, acc, n_drawn);
 }
 
 /* Same, from the input layout: xyz rows, mass, h. */
@@ -823,21 +895,8 @@ int orc_splat_particles(const float *xyz, const float *mass, const float *h, uin
 {
     orc_proj P;
     orc_proj_init(&P, c, rp);
-    int st = ORC_OK;
-    u128 total = 0;
-    uint64_t drawn = 0;
-    for (uint64_t i = 0; i < n; ++i) {
-        orc_splat s;
-        int r = orc_project_one(&P, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], mass[i], h[i], &s);
-        if (r < 0) st = ORC_ERR_RANGE;
-        if (r != 1) continue;
-        total += s.Wq;
-        drawn++;
-        orc_splat_one(&P, &s, c->width, c->height, acc, NULL);
-    }
-    if (total >> 64) st = ORC_ERR_RANGE;
-    if (n_drawn) *n_drawn = drawn;
-    return st;
+    orc_src S = {NULL, NULL, xyz, mass, h, NULL};
+    return orc_splat_src(&P, &S, n, c->width, c->height, acc, n_drawn);
 }
 
 /* Image value at one pixel from a point list (for sampled checks of large images). */
@@ -982,28 +1041,20 @@ int orc_render_lod(const orc_tree *T, const double lo[3], double side, const orc
 {
     uint32_t *sel = (uint32_t *)malloc(sizeof(uint32_t) * (T->n_nodes + 1));
     int64_t m = orc_select(T, lo, side, c, rp, sel);
-    int st = ORC_OK;
-    uint64_t dr = 0, np = 0;
-    orc_proj P;
-    orc_proj_init(&P, c, rp);
-    u128 total = 0;
+    uint64_t np = 0;
+    for (int64_t k = 0; k < m; ++k) np += T->nodes[sel[k]].point_count;
+    uint64_t *rows = (uint64_t *)malloc(sizeof(uint64_t) * (np + 1));
+    uint64_t q = 0;
     for (int64_t k = 0; k < m; ++k) {
         const orc_node *nd = &T->nodes[sel[k]];
-        for (uint64_t j = nd->point_first; j < nd->point_first + nd->point_count; ++j) {
-            orc_splat s;
-            np++;
-            int r = orc_project_one(&P, T->pts4[4 * j], T->pts4[4 * j + 1], T->pts4[4 * j + 2], T->pts4[4 * j + 3],
-                                    T->hs[j], &s);
-            if (r < 0) st = ORC_ERR_RANGE;
-            if (r != 1) continue;
-            total += s.Wq;
-            dr++;
-            orc_splat_one(&P, &s, c->width, c->height, acc, NULL);
-        }
+        for (uint64_t j = nd->point_first; j < nd->point_first + nd->point_count; ++j) rows[q++] = j;
     }
-    if (total >> 64) st = ORC_ERR_RANGE;
+    orc_proj P;
+    orc_proj_init(&P, c, rp);
+    orc_src S = {T->pts4, T->hs, NULL, NULL, NULL, rows};
+    int st = orc_splat_src(&P, &S, np, c->width, c->height, acc, n_drawn);
+    free(rows);
     free(sel);
-    if (n_drawn) *n_drawn = dr;
     if (n_points) *n_points = np;
     return st;
 }

@@ -25,8 +25,11 @@ def build(force: bool = False) -> str:
     """Compile oracle.c with every float operation rounded on its own (no FMA contraction)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
-                               SRC, "-lm", "-o", tmp])
+        base = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared", SRC, "-lm", "-o", tmp]
+        try:  # OpenMP only shares a frame's points out between threads (integer images, order-free)
+            subprocess.check_call(base[:5] + ["-fopenmp"] + base[5:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, LIB)
     return LIB
 
@@ -82,6 +85,8 @@ def lib():
         L.orc_cbrt.argtypes = [C.c_double]
         L.orc_cbrt.restype = C.c_double
         L.orc_kernel_table.argtypes = [C.c_int, i32p]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_get_threads.restype = C.c_int
         L.orc_morton_key.argtypes = [C.c_float, C.c_float, C.c_float, f64p, C.c_double]
         L.orc_morton_key.restype = C.c_uint64
         L.orc_morton_keys.argtypes = [f32p, C.c_uint64, f64p, C.c_double, u64p]
@@ -163,6 +168,15 @@ def neglogs(u) -> np.ndarray:
 
 def cbrt(t: float) -> float:
     return float(lib().orc_cbrt(t))
+
+
+def set_threads(n: int):
+    """Threads of the frame loops (0 = all that OpenMP offers); images do not depend on it."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
 
 
 def kernel_table(kernel: int = 0) -> np.ndarray:

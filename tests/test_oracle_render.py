@@ -274,3 +274,23 @@ def test_pixel_update_count():
     a = np.array([[0.5, 0.5, 0.5, 1.0], [0.45, 0.52, 0.5, 2.0], [0.6, 0.4, 0.55, 0.5]], np.float32)
     ha = np.array([0.01, 0.004, 0.02], np.float32)
     assert O.count_updates(a, ha, cam, rp) == sum(O.count_updates(a[i:i + 1], ha[i:i + 1], cam, rp) for i in range(3))
+
+
+def test_frame_independent_of_thread_count():
+    # the frame loops share points out between threads with images of their own, summed as
+    # integers at the end: one thread and all threads give the same image bit for bit
+    p = synth.tiny(60000, seed=23)
+    T = O.build_tree(p.xyz, p.mass, p.h, seed=3, n_max=300)
+    cam = synth.look_at((0.45, 0.55, -0.4), (0.5, 0.5, 0.5), width=200, height=150)
+    rp = O.rparams(lambda_px=8.0)
+    try:
+        O.set_threads(1)
+        a, st_a, nd_a, _ = O.render_lod(T, cam, rp)
+        ba, _, _ = O.splat_particles(p.xyz, p.mass, p.h, cam, rp)
+        O.set_threads(0)
+        b, st_b, nd_b, _ = O.render_lod(T, cam, rp)
+        bb, _, _ = O.splat_particles(p.xyz, p.mass, p.h, cam, rp)
+    finally:
+        O.set_threads(0)
+    assert st_a == st_b == 0 and nd_a == nd_b and a.sum() > 0
+    assert np.array_equal(a, b) and np.array_equal(ba, bb)
