@@ -379,6 +379,23 @@ typedef enum {
 gblod_status gblod_probe_enable(int32_t kernel);
 gblod_status gblod_probe_read(double *total_ms, uint64_t *launches);
 
+/* Issue-rate probes of the integer instruction mixes the splat kernels execute (the measured
+ * ceilings that roofline fractions of the integer-bound kernels are stated against; the paper has
+ * no counterpart).  Kinds: ALU = (a ^ b) + c chains (2 ops per step), IMAD = 32-bit multiply-add,
+ * IMAD_WIDE = 64-bit accumulation of a 32 x 32 -> 64 product, IMAD_HI = accumulation of the high
+ * word of a 32 x 32 product, LDS = conflict-free shared-memory word loads, RADIAL = the radial
+ * rule's per-pixel body with every pixel inside the support (unit: pixel updates), SEPARABLE = the
+ * separable rule's per-pixel body (unit: pixel updates).  One untimed and one timed launch of
+ * (SMs x resident blocks) x 256 threads, `iters` outer iterations per thread (1..2^24), enqueued
+ * on `stream` and timed with CUDA events; the call waits for them.  Out: *ms = device time of the
+ * timed launch, *units = operations (or pixel updates) it performed.  It allocates (and frees) a
+ * small result buffer with cudaMallocAsync. */
+typedef enum {
+    GBLOD_MB_ALU = 0, GBLOD_MB_IMAD, GBLOD_MB_IMAD_WIDE, GBLOD_MB_IMAD_HI, GBLOD_MB_LDS, GBLOD_MB_RADIAL,
+    GBLOD_MB_SEPARABLE, GBLOD_MB_COUNT_
+} gblod_microbench_kind;
+gblod_status gblod_microbench(int32_t kind, uint32_t iters, void *stream, double *ms, double *units);
+
 const char *gblod_status_string(gblod_status s);
 const char *gblod_last_error(void);
 

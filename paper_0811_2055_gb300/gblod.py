@@ -113,6 +113,7 @@ _L.gblod_diff_backward.argtypes = [_vp, _vp, _vp, _vp, _u64, C.POINTER(Camera), 
 _L.gblod_launch_count.restype = _u64
 _L.gblod_probe_enable.argtypes = [_i32]
 _L.gblod_probe_read.argtypes = [C.POINTER(_d), C.POINTER(_u64)]
+_L.gblod_microbench.argtypes = [_i32, C.c_uint32, _vp, C.POINTER(_d), C.POINTER(_d)]
 _L.gblod_status_string.restype = C.c_char_p
 _L.gblod_status_string.argtypes = [C.c_int]
 _L.gblod_last_error.restype = C.c_char_p
@@ -120,7 +121,8 @@ for _f in ("gblod_build_lod", "gblod_octree_get_info", "gblod_octree_export", "g
            "gblod_render", "gblod_render_bruteforce", "gblod_renderer_status", "gblod_renderer_stats",
            "gblod_renderer_last_selection", "gblod_morton_keys", "gblod_project", "gblod_probe_enable",
            "gblod_probe_read", "gblod_renderer_reserve_batch", "gblod_render_batch", "gblod_autotune_tiles",
-           "gblod_diff_render", "gblod_diff_backward", "gblod_octree_quantize", "gblod_octree_export_block16"):
+           "gblod_diff_render", "gblod_diff_backward", "gblod_octree_quantize", "gblod_octree_export_block16",
+           "gblod_microbench"):
     getattr(_L, _f).restype = C.c_int
 
 
@@ -428,6 +430,17 @@ def probe_read() -> tuple[float, int]:
     ms, n = _d(), _u64()
     _check(_L.gblod_probe_read(C.byref(ms), C.byref(n)), "gblod_probe_read")
     return float(ms.value), int(n.value)
+
+
+MB_ALU, MB_IMAD, MB_IMAD_WIDE, MB_IMAD_HI, MB_LDS, MB_RADIAL, MB_SEPARABLE = range(7)
+
+
+def microbench(kind: int, iters: int = 4096, stream=None) -> tuple[float, float]:
+    """(device ms, operations or pixel updates) of one timed launch of an issue-rate probe."""
+    ms, units = _d(), _d()
+    _check(_L.gblod_microbench(int(kind), int(iters), _stream(stream), C.byref(ms), C.byref(units)),
+           "gblod_microbench")
+    return float(ms.value), float(units.value)
 
 
 def u64(t: torch.Tensor) -> np.ndarray:
