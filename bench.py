@@ -1,11 +1,15 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 level-of-detail renderer (one JSON line on stdout, rank 0).
 
-Workload (default `mid`): 2^24 synthetic particles in 4096 NFW halos + 10% background, octree
-with n_max = 16000, and the 240-frame 1920x1080 helical fly-through.  One step = one pass of the
-whole hot path: build the octree on the device (A1-A5), then render all 240 frames at level of
-detail (R1-R4).  `value` is LOD frames/s over the timed steps (build included).  The same frames
-rendered from every particle (brute force) are timed separately under "all_points".
+Workload (default `paper`): one paper-scale timestep of 150M synthetic particles (65,536 NFW
+halos, a central halo holding 30% of them, 10% uniform background), octree with n_max = 16000,
+and the eight 1920x1080 views from inside the central halo out to the whole box.  One step = one
+pass of the whole hot path: build the octree on the device (A1-A5), then render the eight views
+`--view-repeats` times at level of detail (R1-R4).  `value` is LOD frames/s over the timed steps
+(build included); per view: p50/p99, splats/s and both rooflines (pixel updates against the
+measured per-pixel ceiling, bytes against HBM).  The same views rendered from every particle
+(brute force) are timed under "all_points".  `--workload mid` runs the 2^24-particle 240-frame
+fly-through instead.
 
 --impl reference times the CPU oracle (test infrastructure, plain C) on the host cores instead.
 Multi-GPU (torchrun): every rank runs the full step on its own replica (weak scaling, no
@@ -28,11 +32,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "splats/s & 1080p frames/s (LOD vs all points); p50/p99 frame latency"
-# integer operations of one (splat, pixel) contribution: two subtractions, two squares and an add
-# (squared distance), a multiply and a shift (table index), a compare, a table read, a multiply and a
-# shift (amplitude times table value), an add (accumulation)
+# integer operations of one (splat, pixel) contribution by the rule's definition: two subtractions, two
+# squares and an add (squared distance), a multiply and a shift (table index), a compare, a table read, a
+# multiply and a shift (amplitude times table value), an add (accumulation)
 OPS_PER_PIXEL_UPDATE = 12
-SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
 def args_():
@@ -42,36 +45,40 @@ def args_():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-block16", action="store_true", help="skip the 16-bit block-code fly-through")
-    ap.add_argument("--workload", choices=["mid", "paper", "tiny", "diff", "serve", "paper-views"], default="mid")
+    ap.add_argument("--workload", choices=["paper", "mid", "tiny", "diff", "serve", "paper-views"], default="paper")
+    ap.add_argument("--view-repeats", type=int, default=4, help="paper: passes over the eight views per step")
     ap.add_argument("--repeats", type=int, default=20, help="paper-views: timed repeats per view")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of offered load")
     ap.add_argument("--sessions", type=int, default=64)
     ap.add_argument("--session-budget-gb", type=float, default=4.0)
     ap.add_argument("--frames", type=int, default=0, help="frames per step (0 = the workload's path)")
+    ap.add_argument("--path-frames", type=str, default="", help="mid: comma-separated frames of the 240-frame path")
     ap.add_argument("--particles", type=int, default=0, help="particles (0 = the workload's size)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-brute", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-views", type=int, default=16, help="views per batch in the batched measurement")
-    ap.add_argument("--batch-capacity-log2", type=int, default=29, help="log2 of the batch record capacity")
+    ap.add_argument("--batch-capacity-log2", type=int, default=0,
+                    help="log2 of the batch record capacity (0: 30 for paper, 29 otherwise)")
     return ap.parse_args()
 
 
-def workload(name: str, frames: int, particles: int = 0):
+def workload(name: str, frames: int, particles: int = 0, path_frames: str = ""):
     from paper_0811_2055_gb300 import synth
     if name == "mid":
         p = synth.mid(particles) if particles else synth.mid()
-        nf = frames or 240
-        cams = [synth.helix_view(k * 240 // nf) for k in range(nf)]
+        ks = [int(x) for x in path_frames.split(",") if x.strip()] if path_frames else \
+            [k * 240 // (frames or 240) for k in range(frames or 240)]
+        cams = [synth.helix_view(k) for k in ks]
         desc = (f"mid: {p.n} particles (NFW halos, dN/dM ~ M^-1.9, c in [5,15], + 10% uniform), n_max 16000, "
-                f"{nf}-frame 1920x1080 helical fly-through")
+                + (f"frames {path_frames} of " if path_frames else f"{len(ks)} frames of ")
+                + "the 240-frame 1920x1080 helical fly-through")
     elif name == "paper":
         p = synth.paper_scale(particles) if particles else synth.paper_scale()
-        nf = frames or 8
-        cams = [synth.paper_view(j % 8) for j in range(nf)]
-        desc = ("paper: 150M particles (65,536 NFW halos + central halo with 30% + 10% uniform), n_max 16000, "
-                "8 views at 1920x1080 from inside the central halo out to the whole box")
+        cams = [synth.paper_view(j) for j in range(8)]
+        desc = (f"paper: {p.n} particles (65,536 NFW halos + central halo with 30% + 10% uniform), n_max 16000, "
+                "the 8 views at 1920x1080 at d_j = 0.01 * 150^(j/7) from inside the central halo out to the whole box")
     else:
         p = synth.tiny()
         nf = frames or 1
@@ -162,18 +169,21 @@ def run_ours(a):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    p, cams, n_max, desc = workload(a.workload, a.frames, a.particles)
-    W, H = cams[0]["width"], cams[0]["height"]
+    p, views, n_max, desc = workload(a.workload, a.frames, a.particles, a.path_frames)
+    reps = max(1, a.view_repeats) if a.workload == "paper" else 1
+    cams = [c for _ in range(reps) for c in views]  # the frames of one step
+    nv, nf = len(views), len(cams)
+    W, H = views[0]["width"], views[0]["height"]
     xyz, mass, h = (torch.from_numpy(x).to(dev) for x in (p.xyz, p.mass, p.h))
     r = gblod.Renderer()
     lam = math.sqrt(n_max)
     par = gblod.make_params(lambda_px=lam)
-    # the untimed census frames also count their pixel updates (same frames as the timed ones)
+    # the untimed census frames also count their pixel updates (the same frames as the timed ones)
     par_count = gblod.make_params(lambda_px=lam, count_updates=True)
     img = torch.empty((H, W), dtype=torch.uint8, device=dev)
     acc = torch.empty((H, W), dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    nf = len(cams)
+    hbm = measured_peaks().get("hbm_gbs")
 
     def barrier():
         if world > 1:
@@ -225,32 +235,34 @@ def run_ours(a):
             tot_ms += e0.elapsed_time(e1)
             if out is not None:  # LOD step: build events first
                 build_ms.append(ev[0].elapsed_time(ev[1]))
-                frame_ms += [ev[2 + 2 * k].elapsed_time(ev[3 + 2 * k]) for k in range(nf)]
+                frame_ms.append([ev[2 + 2 * k].elapsed_time(ev[3 + 2 * k]) for k in range(nf)])
                 out.free()
             else:
-                frame_ms += [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(nf)]
+                frame_ms.append([ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(nf)])
         launches = gblod.launch_count() - l0
         pr = gblod.probe_read() if probe is not None else None
         if probe is not None:
             gblod.probe_enable(gblod.K_ANY)
         return tot_ms, frame_ms, build_ms, launches, pr
 
-    # census of one LOD pass and one brute pass (untimed; the counts are deterministic)
+    def per_view(frame_ms):
+        """frame_ms[step][k] -> the times of each view over all steps and repeats"""
+        return [[row[k] for row in frame_ms for k in range(j, nf, nv)] for j in range(nv)]
+
+    # census of one LOD pass and one all-points pass over the views (untimed; the counts are
+    # deterministic, so the timed frames have the same ones)
     tree = lod_step()
-    lod_counts = {"splats": 0, "points": 0, "pixel_updates": 0, "nodes": 0, "pairs": 0, "pairs_captured": 0}
-    for k, cam in enumerate(cams):
+    lod_c = []
+    for cam in views:
         r.render(tree, cam, par_count, image=img, accum=acc)
-        s = r.stats()
-        lod_counts["pairs"] += s["pairs"]
-        if a.workload == "mid" and k * 240 // nf == SPLAT_CAPTURE["path_frame"]:
-            lod_counts["pairs_captured"] = s["pairs"]
-        lod_counts["splats"] += s["splats"]
-        lod_counts["points"] += s["points"]
-        lod_counts["pixel_updates"] += s["pixel_updates"]
-        lod_counts["nodes"] += s["nodes_selected"]
+        lod_c.append(r.stats())
+    all_c = []
+    for cam in (views if not a.no_brute else []):
+        r.render_bruteforce(xyz, mass, h, cam, par_count, image=img, accum=acc)
+        all_c.append(r.stats())
     # visual equivalence (abstract: indistinguishable from a full rendering): LOD vs all points
     vis = []
-    for cam in cams[:: max(1, nf // 8)]:
+    for cam in views[:: max(1, nv // 8)]:
         li, _ = r.render(tree, cam, par)
         bi, _ = r.render_bruteforce(xyz, mass, h, cam, par)
         d = (li.int() - bi.int()).abs().double()
@@ -263,12 +275,21 @@ def run_ours(a):
     tree.free()
     assert r.status() == gblod.OK
 
+    # measured integer ceilings of this GPU (the per-pixel body of the radial rule, every pixel a hit;
+    # and the issue rate of plain 32-bit adds)
+    mb_ms, mb_units = gblod.microbench(gblod.MB_RADIAL, 4096)
+    body_peak = mb_units / (mb_ms / 1e3) / 1e9  # G pixel updates/s
+    alu_ms, alu_units = gblod.microbench(gblod.MB_ALU, 4096)
+    alu_peak = alu_units / (alu_ms / 1e3) / 1e12  # T int32 ops/s
+
     clocks = Clocks(local)
     tot_ms, frame_ms, build_ms, launches, pr = timed(lod_step, 2 + 2 * nf, a.steps, a.warmup, probe=gblod.K_SPLAT)
-    upd = a.steps * lod_counts["pixel_updates"]  # pixel updates of the timed splat launches (census counts)
     ck = clocks.stop()
+    lod_view_ms = per_view(frame_ms)
+    upd_step = reps * sum(c["pixel_updates"] for c in lod_c)  # pixel updates of one step's splat launches
+    rec_step = reps * sum(c["pairs"] for c in lod_c)
 
-    # 16-bit block codes (storage paragraph): the same fly-through drawn from 10-byte points
+    # 16-bit block codes (storage paragraph): the same frames drawn from 10-byte points
     block16 = None
     if not a.no_block16:
         tree = gblod.build_lod(xyz, mass, h, n_max=n_max, seed=1)
@@ -282,7 +303,7 @@ def run_ours(a):
         bytes_q = int(tree.info().device_bytes)
         par_q = gblod.make_params(lambda_px=lam, point_format=gblod.POINTS_BLOCK16)
         vq = []
-        for cam in cams[:: max(1, nf // 8)]:
+        for cam in views[:: max(1, nv // 8)]:
             li, _ = r.render(tree, cam, par_q)
             bi, _ = r.render_bruteforce(xyz, mass, h, cam, par)
             d = (li.int() - bi.int()).abs().double()
@@ -302,8 +323,7 @@ def run_ours(a):
                 r.render(tree, cam, par_q, image=img, accum=acc)
                 ev[2 * k + 1].record()
             torch.cuda.synchronize()
-            ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(nf)]
-            qf_ms += ms
+            qf_ms += [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(nf)]
             qt_ms += ev[0].elapsed_time(ev[-1])
         assert r.status() == gblod.OK
         tree.free()
@@ -315,43 +335,52 @@ def run_ours(a):
                    "vs_all_points_psnr_db_mean": float(np.mean([v[1] for v in vq]))}
 
     brute = None
+    all_view_ms = None
     if not a.no_brute:
-        b_counts = {"splats": 0, "pixel_updates": 0}
-        for cam in cams:
-            r.render_bruteforce(xyz, mass, h, cam, par_count, image=img, accum=acc)
-            s = r.stats()
-            b_counts["splats"] += s["splats"]
-            b_counts["pixel_updates"] += s["pixel_updates"]
         b_ms, b_frames, _, _, _ = timed(brute_step, 2 * nf, a.steps, a.warmup)
+        all_view_ms = per_view(b_frames)
         brute = dict(frames_per_s=a.steps * nf / (b_ms / 1e3), ms_per_frame=b_ms / (a.steps * nf),
-                     splats_per_s=a.steps * b_counts["splats"] / (b_ms / 1e3),
+                     splats_per_s=a.steps * reps * sum(c["splats"] for c in all_c) / (b_ms / 1e3),
                      points_per_s=a.steps * nf * p.n / (b_ms / 1e3),
                      p50_ms=float(np.percentile(b_frames, 50)), p99_ms=float(np.percentile(b_frames, 99)),
-                     splats_per_frame=b_counts["splats"] / nf, pixel_updates_per_frame=b_counts["pixel_updates"] / nf)
+                     splats_per_frame=sum(c["splats"] for c in all_c) / nv,
+                     pixel_updates_per_frame=sum(c["pixel_updates"] for c in all_c) / nv)
+        if hbm:
+            b_bytes = 20.0 * p.n + 17.0 * W * H
+            brute["hbm_bytes_per_frame"] = b_bytes
+            brute["hbm_frac"] = b_bytes / (b_ms / (a.steps * nf) / 1e3) / (hbm * 1e9)
 
     # batched views (one set of launches, no host waits) and its CUDA-graph replay
     batched = None
     if not a.no_batch:
-        nbv = max(1, a.batch_views)
-        bcams = cams[:: max(1, nf // nbv)][:nbv]
-        cap = 1 << a.batch_capacity_log2  # (tile, splat) records, 16 B each (2^29: 8 GiB for 16 views)
+        nbv = max(1, a.batch_views) if a.workload != "paper" else nv
+        bcams = views[:: max(1, nv // nbv)][:nbv]
+        # (tile, splat) records, 16 B each (2^29: 8 GiB; the eight paper-scale views take 2^30: 16 GiB)
+        cap = 1 << (a.batch_capacity_log2 or (30 if a.workload == "paper" else 29))
         tree = gblod.build_lod(xyz, mass, h, n_max=n_max, seed=1)
         bviews = [(tree, c, torch.empty((H, W), dtype=torch.uint8, device=dev),
                    torch.empty((H, W), dtype=torch.int64, device=dev)) for c in bcams]
-        par_b, _ = r.autotune(bviews, gblod.make_params(lambda_px=lam), record_capacity=cap)
+        try:
+            par_b, _ = r.autotune(bviews, gblod.make_params(lambda_px=lam), record_capacity=cap)
+        except gblod.GblodError as e:  # every tile candidate overflowed the capacity: report, do not stop
+            par_b = None
+            batched = {"views": len(bviews), "record_capacity": cap, "status": int(e.code), "error": str(e)}
+            r.status(reset=True)
+            tree.free()
+    if batched is None and not a.no_batch and par_b is not None:
         r.reserve_batch(bviews, par_b, record_capacity=cap)
         r.status(reset=True)
 
-        def ev_time(fn, reps):
+        def ev_time(fn, reps_):
             fn()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            for _ in range(reps):
+            for _ in range(reps_):
                 fn()
             e1.record()
             torch.cuda.synchronize()
-            return e0.elapsed_time(e1) / reps
+            return e0.elapsed_time(e1) / reps_
 
         def singles():
             for (t, c, im, ac) in bviews:
@@ -378,11 +407,11 @@ def run_ours(a):
         del graph
         tree.free()
 
-    # end to end through the public API: pinned host inputs in, u8 frames out, every step
+    # end to end through the public API: pinned host particles in, every u8 frame out, every step
     e2e = None
     if not a.no_e2e:
         hx, hm, hh = (torch.from_numpy(x).pin_memory() for x in (p.xyz, p.mass, p.h))
-        out_h = torch.empty((H, W), dtype=torch.uint8).pin_memory()
+        out_h = torch.empty((nf, H, W), dtype=torch.uint8).pin_memory()
         dx, dm, dh = torch.empty_like(xyz), torch.empty_like(mass), torch.empty_like(h)
 
         def e2e_step():
@@ -390,14 +419,13 @@ def run_ours(a):
             dm.copy_(hm, non_blocking=True)
             dh.copy_(hh, non_blocking=True)
             t = gblod.build_lod(dx, dm, dh, n_max=n_max, seed=1)
-            for cam in cams:
+            for k, cam in enumerate(cams):
                 im, _ = r.render(t, cam, par, image=img, accum=acc)
-                out_h.copy_(im, non_blocking=True)
+                out_h[k].copy_(im, non_blocking=True)
             torch.cuda.synchronize()
             t.free()
 
-        for _ in range(1):
-            e2e_step()
+        e2e_step()
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
@@ -421,9 +449,31 @@ def run_ours(a):
         return
 
     splat_ms, splat_launches = pr
-    achieved = OPS_PER_PIXEL_UPDATE * upd / (splat_ms / 1e3) / 1e12 if splat_ms > 0 else 0.0
-    peak = SMS * LANES * SM_MAX_MHZ * 1e6 / 1e12
-    lod_frame_s = np.sum(frame_ms) / 1e3
+    achieved = a.steps * upd_step / (splat_ms / 1e3) / 1e9 if splat_ms > 0 else 0.0
+    rec_per_launch = a.steps * rec_step / max(splat_launches, 1)
+    lod_frame_s = float(np.sum(frame_ms)) / 1e3
+    vlist = []
+    for j, cam in enumerate(views):
+        lm = lod_view_ms[j]
+        v = {"view": j, "lod_p50_ms": float(np.percentile(lm, 50)), "lod_p99_ms": float(np.percentile(lm, 99)),
+             "lod_fps": 1e3 / float(np.mean(lm)), "lod_splats": int(lod_c[j]["splats"]),
+             "lod_pixel_updates": int(lod_c[j]["pixel_updates"]), "lod_records": int(lod_c[j]["pairs"]),
+             "lod_splats_per_s": lod_c[j]["splats"] / (float(np.mean(lm)) / 1e3),
+             "lod_gupdates_per_s": lod_c[j]["pixel_updates"] / (float(np.mean(lm)) / 1e3) / 1e9}
+        v["lod_frac_of_body_peak"] = v["lod_gupdates_per_s"] / body_peak
+        if hbm:
+            v["lod_hbm_frac"] = (20.0 * lod_c[j]["points"] + 17.0 * W * H) / (float(np.mean(lm)) / 1e3) / (hbm * 1e9)
+        if all_view_ms is not None:
+            am = all_view_ms[j]
+            v.update({"all_p50_ms": float(np.percentile(am, 50)), "all_p99_ms": float(np.percentile(am, 99)),
+                      "all_fps": 1e3 / float(np.mean(am)), "all_splats": int(all_c[j]["splats"]),
+                      "all_pixel_updates": int(all_c[j]["pixel_updates"]),
+                      "all_gupdates_per_s": all_c[j]["pixel_updates"] / (float(np.mean(am)) / 1e3) / 1e9})
+            v["all_frac_of_body_peak"] = v["all_gupdates_per_s"] / body_peak
+            if hbm:
+                v["all_hbm_frac"] = (20.0 * p.n + 17.0 * W * H) / (float(np.mean(am)) / 1e3) / (hbm * 1e9)
+        vlist.append(v)
+    flat = [x for row in frame_ms for x in row]
     line = {
         "metric": METRIC,
         "value": value,
@@ -437,17 +487,15 @@ def run_ours(a):
         "vs_baseline": None,
         "dtype": "f32 projection, u64 fixed-point accumulation, f64 node criterion",
         "data": "synthetic",
-        "config": {"workload": desc, "particles": p.n, "frames_per_step": nf, "resolution": f"{W}x{H}",
-                   "n_max": n_max, "lambda_px": lam, "kernel": "gaussian, sigma = h, 3-sigma support",
-                   "step": "build_lod + every frame at level of detail",
-                   "l2": "flushed between steps (256 MiB write); octree and particles exceed the 129 MB L2",
-                   "octree_nodes": int(info.n_nodes), "octree_points": int(info.n_points)},
+        "config": workload_config(a, p, views, reps, n_max, lam, desc, info),
         "lod": {"frames_per_s_excl_build": a.steps * nf / lod_frame_s,
-                "splats_per_s": a.steps * lod_counts["splats"] / (tot_ms / 1e3),
-                "p50_ms": float(np.percentile(frame_ms, 50)), "p99_ms": float(np.percentile(frame_ms, 99)),
-                "points_per_frame": lod_counts["points"] / nf, "splats_per_frame": lod_counts["splats"] / nf,
-                "nodes_per_frame": lod_counts["nodes"] / nf,
-                "pixel_updates_per_frame": lod_counts["pixel_updates"] / nf},
+                "splats_per_s": a.steps * reps * sum(c["splats"] for c in lod_c) / (tot_ms / 1e3),
+                "p50_ms": float(np.percentile(flat, 50)), "p99_ms": float(np.percentile(flat, 99)),
+                "points_per_frame": sum(c["points"] for c in lod_c) / nv,
+                "splats_per_frame": sum(c["splats"] for c in lod_c) / nv,
+                "nodes_per_frame": sum(c["nodes_selected"] for c in lod_c) / nv,
+                "pixel_updates_per_frame": sum(c["pixel_updates"] for c in lod_c) / nv},
+        "views": vlist,
         "build": {"ms": float(np.median(build_ms)), "particles_per_s": p.n / (np.median(build_ms) / 1e3)},
         "visual_equivalence": visual,
         "all_points": brute,
@@ -456,21 +504,45 @@ def run_ours(a):
         "clocks": ck,
         "e2e": e2e,
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "k_splat_tiles (R3)", "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak if peak else None,
-                     "traffic": splat_traffic(a, lod_counts, nf),
-                     "traffic_note": "DRAM read + write bytes of one ncu capture of the splat kernel (frame "
-                                     f"{SPLAT_CAPTURE['path_frame']} of the 240-frame mid path), scaled to the mean "
-                                     "launch by its (tile, splat) records; null when the kernel source or binning rule "
-                                     "differs from the captured one or the workload is not mid",
+        "roofline": {"kernel": "k_splat_tiles (R3)", "bound": "alu", "achieved": achieved, "peak": body_peak,
+                     "unit": "G pixel updates/s", "frac": achieved / body_peak if body_peak else None,
+                     "traffic": splat_traffic(rec_per_launch),
+                     "peak_note": "measured: the radial rule's per-pixel body (every pixel inside the support, no "
+                                  "list or staging work) on all SMs, gblod_microbench(GBLOD_MB_RADIAL); of measured",
+                     "int32_issue_peak_tops": alu_peak, "ops_per_update": OPS_PER_PIXEL_UPDATE,
+                     "achieved_int32_tops": achieved * OPS_PER_PIXEL_UPDATE / 1e3,
+                     "traffic_note": "DRAM read + write bytes per launch: one ncu capture of the splat kernel, per "
+                                     "(tile, splat) record, times this run's records per launch; null when the "
+                                     "binning rule or the kernel source differs from the captured one",
                      "launches": int(splat_launches), "avg_launch_ms": splat_ms / max(splat_launches, 1),
-                     "peak_note": "152 SMs x 128 lanes x 2070 MHz (no measured ALU peak in MEASURED_PEAKS.json)"},
+                     "records_per_launch": rec_per_launch},
     }
     if not a.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(p, cams, n_max)
+        line["cpu_baseline"] = cpu_baseline(a, p, views, n_max, lod_c, info)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def workload_config(a, p, views, reps, n_max, lam, desc, info=None) -> dict:
+    """The `config` object both arms print for a workload."""
+    c = {"workload": desc, "particles": int(p.n), "views": len(views), "view_repeats_per_step": reps,
+         "frames_per_step": len(views) * reps, "resolution": f"{views[0]['width']}x{views[0]['height']}",
+         "n_max": n_max, "lambda_px": lam, "kernel": "gaussian, sigma = h, 3-sigma support",
+         "step": "build_lod + every frame of the step at level of detail",
+         "l2": "flushed between steps (256 MiB write); particles and octree exceed the 129 MB L2"}
+    if info is not None:  # (nodes, stored points): the GPU octree's info or the oracle tree's sizes
+        c["octree_nodes"], c["octree_points"] = (int(info.n_nodes), int(info.n_points)) \
+            if hasattr(info, "n_nodes") else (int(info[0]), int(info[1]))
+    return c
+
+
+def measured_peaks() -> dict:
+    f = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(f))
+    except (OSError, ValueError):
+        return {}
 
 
 def splat_source(src: bytes) -> bytes:
@@ -484,79 +556,132 @@ def splat_source(src: bytes) -> bytes:
     return src[r0:r1] + src[a:b]
 
 
-# DRAM bytes of one ncu capture of the splat kernel (--set full, default tile; the frame of the 240-frame
-# mid path given by path_frame, drawn by the census pass) and the sha256 of the source text above at the
-# time of the capture; the ncu summary under profiles/ lists the same numbers.
+# DRAM bytes of one ncu capture of the splat kernel (--set full, default tile, one launch: the frame of the
+# 240-frame mid path given by path_frame, drawn by the census pass), the (tile, splat) records that launch
+# splatted, and the sha256 of the source text above at the time of the capture; the ncu summary under
+# profiles/ lists the same numbers.
 SPLAT_CAPTURE = {"source_sha256": "84df3723180f4af9614404d5e02fe1e2dca24577cac86f10ade50dbcdcdf77e1",
-                 "path_frame": 160, "dram_read_bytes": 444.259840e6, "dram_write_bytes": 16.311552e6}
+                 "path_frame": 160, "records": 0, "dram_read_bytes": 444.259840e6, "dram_write_bytes": 16.311552e6}
 
 
-def splat_traffic(a, lod_counts, nf):
-    """DRAM bytes per splat launch: the capture above, scaled to the mean launch of this run by its (tile,
-    splat) records; None if the kernel source differs from the captured one or the workload is not mid."""
+def splat_traffic(records_per_launch: float):
+    """DRAM bytes per splat launch: the capture above per record, times this run's records per launch;
+    None if the kernel source differs from the captured one or the capture has no record count."""
     import hashlib
-    root = os.path.dirname(os.path.abspath(__file__))
     try:
-        src = open(os.path.join(root, "paper_0811_2055_gb300", "csrc", "render.cu"), "rb").read()
+        src = open(os.path.join(ROOT, "paper_0811_2055_gb300", "csrc", "render.cu"), "rb").read()
     except OSError:
         return None
     if hashlib.sha256(splat_source(src)).hexdigest() != SPLAT_CAPTURE["source_sha256"]:
         return None
-    if a.workload != "mid" or a.particles or not lod_counts["pairs_captured"]:
+    if not SPLAT_CAPTURE["records"] or not records_per_launch:
         return None
     captured = SPLAT_CAPTURE["dram_read_bytes"] + SPLAT_CAPTURE["dram_write_bytes"]
-    return captured * (lod_counts["pairs"] / nf) / lod_counts["pairs_captured"]
+    return captured / SPLAT_CAPTURE["records"] * records_per_launch
 
 
 # ------------------------------------------------------------------ the oracle (CPU)
 
-def cpu_baseline(p, cams, n_max, frame_steps: int = 1):
-    """Oracle build of the full particle set + LOD render of one frame, extrapolated to a step."""
+def _oracle_threads_all() -> int:
     from oracle import oracle as O
+    O.set_threads(0)
+    return O.get_threads()
+
+
+def cpu_baseline(a, p, views, n_max, lod_c, info):
+    """The oracle (test infrastructure, plain C) on the host cores, on a bounded sample of the same
+    workload: it builds the octree of every 16th particle (1 thread; build time scaled to all
+    particles by their count) and draws the sample octree's frames of the last two views at 1 thread
+    and at all threads; its pixel-update rate (updates of the sample frames over their time) then
+    prices the full workload's frames, whose update counts the census gave (the oracle's frames are
+    bit-identical).  Returns the frames/s of one step of the full workload at all threads."""
+    from oracle import oracle as O
+    from paper_0811_2055_gb300 import synth
+    k = 16
+    sub = p.subset(np.arange(0, p.n, k))
+    O.set_threads(1)
     t0 = time.perf_counter()
-    T = O.build_tree(p.xyz, p.mass, p.h, seed=1, n_max=n_max)
+    T = O.build_tree(sub.xyz, sub.mass, sub.h, seed=1, n_max=n_max)
     t_build = time.perf_counter() - t0
-    k = len(cams) // 2
     rp = O.rparams(lambda_px=math.sqrt(n_max))
-    t0 = time.perf_counter()
-    for _ in range(frame_steps):
-        O.render_lod(T, cams[k], rp)
-    t_frame = (time.perf_counter() - t0) / frame_steps
-    nf = len(cams)
-    return {"value": nf / (t_build + nf * t_frame), "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": f"one oracle build of all {p.n} particles ({t_build:.1f} s) + LOD frame {k} of the path "
-                      f"({t_frame:.1f} s), extrapolated to build + {nf} frames"}
+    vs = views[-2:]
+    rates = {}
+    for th in (1, 0):
+        O.set_threads(th)
+        upd, secs = 0, 0.0
+        for cam in vs:
+            c = dict(cam, width=cam["width"] // 4, height=cam["height"] // 4, f_px=cam["f_px"] / 4,
+                     cx=cam["cx"] / 4, cy=cam["cy"] / 4) if th == 1 else cam
+            t0 = time.perf_counter()
+            _, _, _, _, nu = O.render_lod_counted(T, c, rp)
+            secs += time.perf_counter() - t0
+            upd += nu
+        rates[th] = upd / secs
+    cores = _oracle_threads_all()
+    reps = a.view_repeats if a.workload == "paper" else 1
+    step_upd = reps * sum(c["pixel_updates"] for c in lod_c)
+    t_step = t_build * k + step_upd / rates[0]
+    O.set_threads(0)
+    return {"value": reps * len(views) / t_step, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle octree of every {k}th particle ({sub.n}; 1-thread build {t_build:.1f} s, x{k} for all "
+                      f"particles) and its LOD frames of views {len(views) - 2}..{len(views) - 1} (1 thread at "
+                      f"quarter resolution, all {cores} threads at full resolution); the all-thread pixel-update "
+                      f"rate prices the step's {step_upd:.3g} census updates",
+            "updates_per_s_1_thread": rates[1], "updates_per_s_all_threads": rates[0],
+            "build_s_1_thread_estimated_all_particles": t_build * k}
+
+
+def band_rows(H: int, b: int, nb: int) -> tuple[int, int]:
+    """Rows [b H/nb, (b+1) H/nb) of a frame of height H."""
+    bh = H // nb
+    return b * bh, (b + 1) * bh
 
 
 def run_reference(a):
+    """The CPU oracle on the same workload and metric.  Setup (untimed, reported): the oracle builds
+    the octree of every particle.  Each step draws one horizontal band of 1/36 of one view's rows
+    (the oracle's row window: the whole frame's selection and projection with the pixel loops limited
+    to the band, so the band is exactly those rows of the frame), cycling over views and bands; value
+    = frames drawn (band fractions) / time."""
     rank, world, _ = dist_info()
     if rank != 0:
         return
     from oracle import oracle as O
-    p, cams, n_max, desc = workload(a.workload, a.frames, a.particles)
+    p, views, n_max, desc = workload(a.workload, a.frames, a.particles, a.path_frames)
+    reps = max(1, a.view_repeats) if a.workload == "paper" else 1
+    lam = math.sqrt(n_max)
+    cores = _oracle_threads_all()
     t0 = time.perf_counter()
     T = O.build_tree(p.xyz, p.mass, p.h, seed=1, n_max=n_max)
     t_build = time.perf_counter() - t0
-    rp = O.rparams(lambda_px=math.sqrt(n_max))
-    nf = len(cams)
-    order = [(nf // 2 + 37 * i) % nf for i in range(a.warmup + a.steps)]
-    for i in range(a.warmup):
-        O.render_lod(T, cams[order[i]], rp)
+    rp = O.rparams(lambda_px=lam)
+    H = views[0]["height"]
+    nb = 36 if H % 36 == 0 else 1
+    bh = H // nb
+
+    def band(s):
+        r0, r1 = band_rows(H, (7 * s + 11 * (s // len(views))) % nb, nb)
+        return O.render_lod_rows(T, views[s % len(views)], rp, r0, r1)
+
+    for s in range(a.warmup):
+        band(s)
     ts = []
-    for i in range(a.steps):
+    for s in range(a.warmup, a.warmup + a.steps):
         t0 = time.perf_counter()
-        O.render_lod(T, cams[order[a.warmup + i]], rp)
+        band(s)
         ts.append(time.perf_counter() - t0)
-    t_frame = float(np.mean(ts))
-    value = nf / (t_build + nf * t_frame)
-    sample = (f"oracle (plain C, 1 thread): one build of all {p.n} particles ({t_build:.1f} s) and one LOD frame "
-              f"per step ({t_frame:.1f} s mean over {a.steps} frames), extrapolated to build + {nf} frames")
+    frac = bh / H
+    value = a.steps * frac / sum(ts)
+    sample = (f"oracle (plain C, {cores} threads): octree of all {p.n} particles built once before the steps "
+              f"({t_build:.1f} s, 1 thread, not in the steps); each step draws a band of {bh} of the {H} rows of one "
+              f"view ({frac:.4f} of a frame), cycling over views and bands")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": (t_build + nf * t_frame) * 1e3,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * float(np.mean(ts)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 oracle, f32 projection",
-            "data": "synthetic", "config": {"workload": desc, "particles": p.n, "frames_per_step": nf,
-                                            "n_max": n_max},
-            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": workload_config(a, p, views, reps, n_max, lam, desc,
+                                                           (len(T.nodes), int(T.hs.shape[0]))),
+            "oracle_build_s": t_build,
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -666,6 +666,7 @@ int orc_build_topdown(const float *xyz, const uint32_t *ids, uint64_t n, uint32_
 typedef struct {
     float ex, ey, ez, rx, ry, rz, ux, uy, uz, fx, fy, fz;
     float F, CX, CY, ZN, smin, smax, A, B, Rk, Wimg, Himg;
+    int32_t row0, row1; /* image rows drawn: [row0, row1) (the whole image unless a window is asked for) */
     int32_t K[ORC_T];
 } orc_proj;
 
@@ -693,6 +694,8 @@ static void orc_proj_init(orc_proj *P, const orc_camera *c, const orc_rparams *r
     P->Rk = rp->kernel == 1 ? 2.0f : 3.0f;
     P->Wimg = (float)c->width;
     P->Himg = (float)c->height;
+    P->row0 = 0;
+    P->row1 = c->height;
     orc_kernel_table(rp->kernel, P->K);
 }
 
@@ -761,10 +764,11 @@ static void orc_splat_one(const orc_proj *P, const orc_splat *s, int W, int H, u
     int64_t r256 = (int64_t)sqrt(qlim) + 256;
     int64_t x0 = ((int64_t)s->U - 128 - r256) / 256 - 1, x1 = ((int64_t)s->U - 128 + r256) / 256 + 1;
     int64_t y0 = ((int64_t)s->V - 128 - r256) / 256 - 1, y1 = ((int64_t)s->V - 128 + r256) / 256 + 1;
+    (void)H;
     if (x0 < 0) x0 = 0;
-    if (y0 < 0) y0 = 0;
+    if (y0 < P->row0) y0 = P->row0;
     if (x1 > W - 1) x1 = W - 1;
-    if (y1 > H - 1) y1 = H - 1;
+    if (y1 > P->row1 - 1) y1 = P->row1 - 1;
     for (int64_t py = y0; py <= y1; ++py) {
         for (int64_t px = x0; px <= x1; ++px) {
             int64_t ddx = px * 256 + 128 - (int64_t)s->U;
@@ -774,7 +778,7 @@ static void orc_splat_one(const orc_proj *P, const orc_splat *s, int W, int H, u
             u128 idx = qs >> 37;
             if (idx < ORC_T) {
                 u128 c = ((u128)s->Wq * (u128)(uint32_t)P->K[(int)idx]) >> 16;
-                if (acc) acc[py * W + px] += (uint64_t)c;
+                if (acc) acc[(py - P->row0) * W + px] += (uint64_t)c;
                 if (updates) ++*updates;
             }
         }
@@ -819,15 +823,16 @@ static void orc_src_get(const orc_src *S, uint64_t k, float *x, float *y, float 
  * point's amplitude was out of range or the sum of drawn amplitudes reached 2^64 (a pixel could
  * then wrap). */
 static int orc_splat_src(const orc_proj *P, const orc_src *S, uint64_t n, int W, int H, uint64_t *acc,
-                         uint64_t *n_drawn)
+                         uint64_t *n_drawn, uint64_t *n_updates)
 {
     int T = orc_get_threads();
     if (T > 64) T = 64;
-    size_t npix = (size_t)W * (size_t)H;
+    (void)H;
+    size_t npix = (size_t)W * (size_t)(P->row1 - P->row0);
     uint64_t *img = (uint64_t *)calloc((size_t)T * npix, sizeof(uint64_t));
     int bad[64] = {0};
     u128 tot[64] = {0};
-    uint64_t dr[64] = {0};
+    uint64_t dr[64] = {0}, up[64] = {0};
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(T) schedule(dynamic, 4096)
 #endif
@@ -845,16 +850,18 @@ static int orc_splat_src(const orc_proj *P, const orc_src *S, uint64_t n, int W,
         if (r != 1) continue;
         tot[t] += s.Wq;
         dr[t]++;
-        orc_splat_one(P, &s, W, H, img + (size_t)t * npix, NULL);
+        orc_splat_one(P, &s, W, H, img + (size_t)t * npix, n_updates ? &up[t] : NULL);
     }
     int st = ORC_OK;
     u128 total = 0;
-    uint64_t drawn = 0;
+    uint64_t drawn = 0, updates = 0;
     for (int t = 0; t < T; ++t) {
         if (bad[t]) st = ORC_ERR_RANGE;
         total += tot[t];
         drawn += dr[t];
+        updates += up[t];
     }
+    if (n_updates) *n_updates = updates;
     for (size_t i = 0; i < npix; ++i)
         for (int t = 0; t < T; ++t) acc[i] += img[(size_t)t * npix + i];
     free(img);
@@ -871,7 +878,7 @@ int orc_splat_points(const float *pts4, const float *hs, uint64_t n, const orc_c
     orc_proj P;
     orc_proj_init(&P, c, rp);
     orc_src S = {pts4, hs, NULL, NULL, NULL, NULL};
-    return orc_splat_src(&P, &S, n, c->width, c->height, acc, n_drawn);
+    return orc_splat_src(&P, &S, n, c->width, c->height, acc, n_drawn, NULL);
 }
 
 /* Same, from the input layout: xyz rows, mass, h. */
@@ -896,7 +903,7 @@ int orc_splat_particles(const float *xyz, const float *mass, const float *h, uin
     orc_proj P;
     orc_proj_init(&P, c, rp);
     orc_src S = {NULL, NULL, xyz, mass, h, NULL};
-    return orc_splat_src(&P, &S, n, c->width, c->height, acc, n_drawn);
+    return orc_splat_src(&P, &S, n, c->width, c->height, acc, n_drawn, NULL);
 }
 
 /* Image value at one pixel from a point list (for sampled checks of large images). */
@@ -1036,11 +1043,15 @@ int64_t orc_select(const orc_tree *T, const double lo[3], double side, const orc
 }
 
 /* LOD render: the brute-force image of exactly the points stored in the selected nodes. */
-int orc_render_lod(const orc_tree *T, const double lo[3], double side, const orc_camera *c, const orc_rparams *rp,
-                   uint64_t *acc, uint64_t *n_drawn, uint64_t *n_points)
+/* Draws the points stored in the nodes sel[0..m) (rows [row0, row1) of the image; acc holds
+ * width * (row1 - row0) values). */
+static int orc_render_nodes(const orc_tree *T, const uint32_t *sel, int64_t m, const orc_camera *c,
+                            const orc_rparams *rp, int32_t row0, int32_t row1, uint64_t *acc, uint64_t *n_drawn,
+                            uint64_t *n_points, uint64_t *n_updates)
 {
-    uint32_t *sel = (uint32_t *)malloc(sizeof(uint32_t) * (T->n_nodes + 1));
-    int64_t m = orc_select(T, lo, side, c, rp, sel);
+    if (row0 < 0) row0 = 0;
+    if (row1 > c->height) row1 = c->height;
+    if (row1 < row0) row1 = row0;
     uint64_t np = 0;
     for (int64_t k = 0; k < m; ++k) np += T->nodes[sel[k]].point_count;
     uint64_t *rows = (uint64_t *)malloc(sizeof(uint64_t) * (np + 1));
@@ -1051,12 +1062,58 @@ int orc_render_lod(const orc_tree *T, const double lo[3], double side, const orc
     }
     orc_proj P;
     orc_proj_init(&P, c, rp);
+    P.row0 = row0;
+    P.row1 = row1;
     orc_src S = {T->pts4, T->hs, NULL, NULL, NULL, rows};
-    int st = orc_splat_src(&P, &S, np, c->width, c->height, acc, n_drawn);
+    int st = orc_splat_src(&P, &S, np, c->width, c->height, acc, n_drawn, n_updates);
     free(rows);
-    free(sel);
     if (n_points) *n_points = np;
     return st;
+}
+
+/* Rows [row0, row1) of the LOD frame (acc holds width * (row1 - row0) values): the same
+ * selection, projection and per-pixel rule as the whole frame, with the pixel loops limited to
+ * those rows, so the result is exactly those rows of the whole frame. */
+int orc_render_lod_rows(const orc_tree *T, const double lo[3], double side, const orc_camera *c,
+                        const orc_rparams *rp, int32_t row0, int32_t row1, uint64_t *acc, uint64_t *n_drawn,
+                        uint64_t *n_points, uint64_t *n_updates)
+{
+    uint32_t *sel = (uint32_t *)malloc(sizeof(uint32_t) * (T->n_nodes + 1));
+    int64_t m = orc_select(T, lo, side, c, rp, sel);
+    int st = orc_render_nodes(T, sel, m, c, rp, row0, row1, acc, n_drawn, n_points, n_updates);
+    free(sel);
+    return st;
+}
+
+/* Part `part` of `n_parts` of a split frame: of the nodes the frame selects, only those whose index
+ * in the node table is congruent to `part` modulo `n_parts` are drawn.  Summing the parts' images
+ * as integers gives the whole frame (each selected node is drawn by exactly one part). */
+int orc_render_lod_part(const orc_tree *T, const double lo[3], double side, const orc_camera *c,
+                        const orc_rparams *rp, int32_t part, int32_t n_parts, uint64_t *acc, uint64_t *n_drawn,
+                        uint64_t *n_points)
+{
+    uint32_t *sel = (uint32_t *)malloc(sizeof(uint32_t) * (T->n_nodes + 1));
+    int64_t m = orc_select(T, lo, side, c, rp, sel), k = 0;
+    for (int64_t j = 0; j < m; ++j)
+        if (n_parts <= 1 || (int64_t)(sel[j] % (uint32_t)n_parts) == part) sel[k++] = sel[j];
+    int st = orc_render_nodes(T, sel, k, c, rp, 0, c->height, acc, n_drawn, n_points, NULL);
+    free(sel);
+    return st;
+}
+
+/* The whole frame, with its pixel-update count. */
+int orc_render_lod_counted(const orc_tree *T, const double lo[3], double side, const orc_camera *c,
+                           const orc_rparams *rp, uint64_t *acc, uint64_t *n_drawn, uint64_t *n_points,
+                           uint64_t *n_updates)
+{
+    return orc_render_lod_rows(T, lo, side, c, rp, 0, c->height, acc, n_drawn, n_points, n_updates);
+}
+
+/* The whole frame. */
+int orc_render_lod(const orc_tree *T, const double lo[3], double side, const orc_camera *c, const orc_rparams *rp,
+                   uint64_t *acc, uint64_t *n_drawn, uint64_t *n_points)
+{
+    return orc_render_lod_rows(T, lo, side, c, rp, 0, c->height, acc, n_drawn, n_points, NULL);
 }
 
 /* ------------------------------------------------------------------ 16-bit block codes */

@@ -116,6 +116,15 @@ def lib():
         L.orc_select.restype = C.c_int64
         L.orc_render_lod.argtypes = [P(Tree), f64p, C.c_double, P(Camera), P(RParams), u64p, P(C.c_uint64),
                                      P(C.c_uint64)]
+        L.orc_render_lod_counted.argtypes = [P(Tree), f64p, C.c_double, P(Camera), P(RParams), u64p,
+                                             P(C.c_uint64), P(C.c_uint64), P(C.c_uint64)]
+        L.orc_render_lod_counted.restype = C.c_int
+        L.orc_render_lod_rows.argtypes = [P(Tree), f64p, C.c_double, P(Camera), P(RParams), C.c_int32, C.c_int32,
+                                          u64p, P(C.c_uint64), P(C.c_uint64), P(C.c_uint64)]
+        L.orc_render_lod_rows.restype = C.c_int
+        L.orc_render_lod_part.argtypes = [P(Tree), f64p, C.c_double, P(Camera), P(RParams), C.c_int32, C.c_int32,
+                                          u64p, P(C.c_uint64), P(C.c_uint64)]
+        L.orc_render_lod_part.restype = C.c_int
         L.orc_render_lod.restype = C.c_int
         L.orc_tonemap.argtypes = [u64p, C.c_uint64, P(RParams), np.ctypeslib.ndpointer(np.uint8, flags="C")]
         L.orc_constants.argtypes = [np.ctypeslib.ndpointer(np.float32, flags="C")]
@@ -331,6 +340,33 @@ def render_lod(tree: OracleTree, cam: dict, rp: RParams):
     nd, npnt = C.c_uint64(), C.c_uint64()
     st = lib().orc_render_lod(tree._ptr, tree.lo, tree.side, C.byref(camera(cam)), C.byref(rp), acc, C.byref(nd),
                               C.byref(npnt))
+    return acc.reshape(cam["height"], cam["width"]), st, int(nd.value), int(npnt.value)
+
+
+def render_lod_counted(tree: OracleTree, cam: dict, rp: RParams):
+    """render_lod plus the frame's pixel updates ((splat, pixel) pairs inside the support)."""
+    acc = np.zeros(cam["height"] * cam["width"], np.uint64)
+    nd, npnt, nu = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    st = lib().orc_render_lod_counted(tree._ptr, tree.lo, tree.side, C.byref(camera(cam)), C.byref(rp), acc,
+                                      C.byref(nd), C.byref(npnt), C.byref(nu))
+    return acc.reshape(cam["height"], cam["width"]), st, int(nd.value), int(npnt.value), int(nu.value)
+
+
+def render_lod_rows(tree: OracleTree, cam: dict, rp: RParams, row0: int, row1: int):
+    """Rows [row0, row1) of render_lod's frame (the same values), with the frame's counts for those rows."""
+    acc = np.zeros((row1 - row0) * cam["width"], np.uint64)
+    nd, npnt, nu = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    st = lib().orc_render_lod_rows(tree._ptr, tree.lo, tree.side, C.byref(camera(cam)), C.byref(rp), int(row0),
+                                   int(row1), acc, C.byref(nd), C.byref(npnt), C.byref(nu))
+    return acc.reshape(row1 - row0, cam["width"]), st, int(nd.value), int(npnt.value), int(nu.value)
+
+
+def render_lod_part(tree: OracleTree, cam: dict, rp: RParams, part: int, n_parts: int):
+    """Part `part` of `n_parts` of render_lod's frame: the selected nodes with index = part (mod n_parts)."""
+    acc = np.zeros(cam["height"] * cam["width"], np.uint64)
+    nd, npnt = C.c_uint64(), C.c_uint64()
+    st = lib().orc_render_lod_part(tree._ptr, tree.lo, tree.side, C.byref(camera(cam)), C.byref(rp), int(part),
+                                   int(n_parts), acc, C.byref(nd), C.byref(npnt))
     return acc.reshape(cam["height"], cam["width"]), st, int(nd.value), int(npnt.value)
 
 

@@ -294,3 +294,17 @@ def test_frame_independent_of_thread_count():
         O.set_threads(0)
     assert st_a == st_b == 0 and nd_a == nd_b and a.sum() > 0
     assert np.array_equal(a, b) and np.array_equal(ba, bb)
+
+
+def test_lod_update_count_equals_the_point_list_count():
+    p = synth.tiny(30000, seed=24)
+    T = O.build_tree(p.xyz, p.mass, p.h, seed=3, n_max=300)
+    cam = synth.look_at((0.5, 0.45, -0.6), (0.5, 0.5, 0.5), width=160, height=120)
+    rp = O.rparams(lambda_px=6.0)
+    acc, st, nd, npts, nu = O.render_lod_counted(T, cam, rp)
+    sel = O.select(T, cam, rp)
+    rows = np.concatenate([np.arange(int(T.nodes[i]["point_first"]), int(T.nodes[i]["point_first"]) +
+                                     int(T.nodes[i]["point_count"])) for i in sel])
+    assert st == 0 and npts == len(rows) and nu > 0
+    assert nu == O.count_updates(T.pts4[rows], T.hs[rows], cam, rp)
+    assert np.array_equal(acc, O.render_lod(T, cam, rp)[0])
