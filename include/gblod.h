@@ -224,6 +224,48 @@ void gblod_renderer_destroy(gblod_renderer *r);
 gblod_status gblod_render(gblod_renderer *r, const gblod_octree *octree, const gblod_camera *camera,
                           const gblod_render_params *params, uint8_t *d_image, uint64_t *d_accum, void *stream);
 
+/* Fitting a node's stored points (abstract: an LOD image "indistinguishable from a full
+ * rendering"; octree paragraph: a node's n points stand for all of its particles).
+ *
+ * gblod_octree_node_points copies node `node`'s stored points (its n_max representatives, or a
+ * leaf's particles) to d_pts4 (count x 4 float: x, y, z, weight) and d_hs (count float), device to
+ * device, on `stream`; either may be NULL to ask for *count (= the node's point_count) only.
+ * gblod_octree_node_members copies the input indices (or ids) of the node's member particles, in
+ * (key, id) order, to d_ids (count uint32; NULL: *count only).
+ * gblod_octree_set_points overwrites the node's stored points with `count` new ones (count must
+ * equal its point_count; d_pts4 count x 4 float, d_hs count float, device pointers).  The node's
+ * particle bounds (bmin, bmax) and h_cull, and those of every ancestor, grow to cover the new
+ * points (a coordinate or h enters the bounds as v + 0, so -0 counts as +0), so culling stays
+ * conservative; the written points' pt_src entries become 0xFFFFFFFF (they copy no particle);
+ * w_rep keeps the subselection's weight while each written point carries its own weight; 16-bit
+ * block codes, if present, are dropped (run gblod_octree_quantize again).  All three wait for
+ * `stream`.  GBLOD_ERR_INVALID_ARG for a node index out of range, a wrong count, or an octree
+ * without fp32 points. */
+gblod_status gblod_octree_node_points(const gblod_octree *octree, uint32_t node, float *d_pts4, float *d_hs,
+                                      uint32_t *count, void *stream);
+gblod_status gblod_octree_node_members(const gblod_octree *octree, uint32_t node, uint32_t *d_ids,
+                                       uint32_t *count, void *stream);
+gblod_status gblod_octree_set_points(gblod_octree *octree, uint32_t node, const float *d_pts4, const float *d_hs,
+                                     uint32_t count, void *stream);
+
+/* One part of a split frame (multi-GPU sharding of one LOD frame, replica octrees on every GPU).
+ * The frame's node selection (depth paragraph) is computed in full; of the nodes it emits, part
+ * `part` of `n_parts` keeps those whose index in the octree's node table is congruent to `part`
+ * modulo `n_parts` (the same on every replica, since the node table is deterministic), and draws
+ * only their points into d_accum (height x width uint64, overwritten).  The parts' images sum, as
+ * integers, to exactly the frame gblod_render draws: every emitted node belongs to one part and the
+ * accumulation is an exact integer sum.  Sum the parts (one int64 sum-reduce, e.g. NCCL), then call
+ * gblod_tonemap once.  GBLOD_ERR_INVALID_ARG unless 0 <= part < n_parts and d_accum is given. */
+gblod_status gblod_render_part(gblod_renderer *r, const gblod_octree *octree, const gblod_camera *camera,
+                               const gblod_render_params *params, int32_t part, int32_t n_parts, uint64_t *d_accum,
+                               void *stream);
+
+/* R4 alone: the log tone map of a caller's accumulation image d_accum (height x width uint64, e.g.
+ * the summed parts of a split frame) into d_image (height x width uint8), with the tone-map fields
+ * of `params` (automatic or fixed range), exactly as gblod_render maps its own accumulation. */
+gblod_status gblod_tonemap(gblod_renderer *r, const uint64_t *d_accum, int32_t width, int32_t height,
+                           const gblod_render_params *params, uint8_t *d_image, void *stream);
+
 /* Brute-force frame: R2-R4 over every particle (d_xyz n x 3, d_mass n, d_h n), no tree
  * (params->point_format is ignored: the fp32 particles are drawn). */
 gblod_status gblod_render_bruteforce(gblod_renderer *r, const float *d_xyz, const float *d_mass, const float *d_h,
@@ -331,8 +373,10 @@ gblod_status gblod_diff_backward(gblod_renderer *r, const float *d_xyz, const fl
  *   - d_accum is required (the caller owns the height x width uint64 output); d_image may be NULL;
  *   - scratch is one statically sized device array inside this library, GBLOD_NOALLOC_SCRATCH_BYTES
  *     bytes, which every GPU that loads the library holds until the process exits;
- *   - the first call on a device also performs that device's set-up (resolves the array's device
- *     address and uploads the kernel table); make that first call before any stream capture;
+ *   - the first call on a device also performs that device's set-up (loads the library's device
+ *     code and uploads the kernel table); make that first call before any stream capture.  Every
+ *     call looks the array's device address up again in the current context (cudaGetSymbolAddress),
+ *     so the entry point stays valid across a teardown and re-creation of the device context;
  *   - frames are limited to GBLOD_NOALLOC_MAX_TILES screen tiles (e.g. 4096 x 4096 pixels with
  *     the default 64 x 16 tiles; larger images are rejected with GBLOD_ERR_INVALID_ARG) and to
  *     GBLOD_NOALLOC_MAX_RECORDS (tile, splat) records (a frame that needs more returns

@@ -226,6 +226,32 @@ gblod_status gblod_render(gblod_renderer *r, const gblod_octree *octree, const g
     });
 }
 
+gblod_status gblod_render_part(gblod_renderer *r, const gblod_octree *octree, const gblod_camera *camera,
+                               const gblod_render_params *params, int32_t part, int32_t n_parts, uint64_t *d_accum,
+                               void *stream)
+{
+    return guarded([&] {
+        if (!r || !octree) fail(GBLOD_ERR_INVALID_ARG, "renderer and octree must not be NULL");
+        if (!d_accum) fail(GBLOD_ERR_INVALID_ARG, "gblod_render_part needs d_accum (the partial image)");
+        if (n_parts < 1 || part < 0 || part >= n_parts) fail(GBLOD_ERR_INVALID_ARG, "need 0 <= part < n_parts");
+        check_camera(camera);
+        const gblod_render_params p = check_params(params);
+        render_lod(r, octree, *camera, p, nullptr, d_accum, (cudaStream_t)stream, (uint32_t)part, (uint32_t)n_parts);
+    });
+}
+
+gblod_status gblod_tonemap(gblod_renderer *r, const uint64_t *d_accum, int32_t width, int32_t height,
+                           const gblod_render_params *params, uint8_t *d_image, void *stream)
+{
+    return guarded([&] {
+        if (!r || !d_accum || !d_image) fail(GBLOD_ERR_INVALID_ARG, "renderer, d_accum and d_image must not be NULL");
+        if (width < 1 || height < 1 || width > 16384 || height > 16384)
+            fail(GBLOD_ERR_INVALID_ARG, "width/height must be in 1..16384");
+        const gblod_render_params p = check_params(params);
+        tonemap_image(r, d_accum, width, height, p, d_image, (cudaStream_t)stream);
+    });
+}
+
 gblod_status gblod_render_bruteforce(gblod_renderer *r, const float *d_xyz, const float *d_mass, const float *d_h,
                                      uint64_t n, const gblod_camera *camera, const gblod_render_params *params,
                                      uint8_t *d_image, uint64_t *d_accum, void *stream)

@@ -59,6 +59,8 @@ template <class T> struct DBuf {
     {
         if (n <= cap) return;
         if (p) A.put(p, cap * sizeof(T), s);
+        p = nullptr; // a failing allocation below leaves an empty buffer, not a released one
+        cap = 0;
         size_t want = n + n / 4 + 64;
         p = static_cast<T *>(A.get(want * sizeof(T), s));
         cap = want;
@@ -138,7 +140,18 @@ int persistent_blocks(int per_sm);
 
 // ------------------------------------------------------------------ scans (scan.cu)
 // Exclusive prefix sums in place-free form: out[i] = sum_{k<i} in[k]; if total != nullptr the
-// grand total is written there (device pointer).  `tmp` is grown as needed.
+// grand total is written there (device pointer).  `tmp` is grown as needed, to at most
+// scan_temp_bytes(n, sizeof element): it is never grown when it already holds that many bytes.
+constexpr size_t SCAN_TILE_ELEMS = 2048; // elements per scan block (256 threads x 8)
+constexpr size_t scan_temp_bytes(size_t n, size_t elem)
+{
+    size_t need = 0, m = n;
+    while (m > SCAN_TILE_ELEMS) {
+        m = (m + SCAN_TILE_ELEMS - 1) / SCAN_TILE_ELEMS;
+        need += 2 * m * elem + 512;
+    }
+    return need + 1024;
+}
 struct ScanTmp {
     DBuf<unsigned char> buf;
 };

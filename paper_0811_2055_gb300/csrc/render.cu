@@ -297,10 +297,13 @@ __global__ void k_select_init(uint32_t *front, uint32_t *cnt)
     cnt[0] = 1u;
 }
 
+// One level of the walk.  Emitted nodes are kept only if they belong to this part of a split frame
+// (node index mod n_parts == part; n_parts = 1 keeps every one); refined nodes are walked either way.
 __global__ void __launch_bounds__(RT) k_select_level(const gblod_node *__restrict__ nodes, Frustum fr,
                                                      const uint32_t *__restrict__ fin, const uint32_t *nin,
                                                      uint32_t *__restrict__ fout, uint32_t *nout,
-                                                     uint32_t *__restrict__ sel, uint32_t *nsel)
+                                                     uint32_t *__restrict__ sel, uint32_t *nsel, uint32_t part,
+                                                     uint32_t n_parts)
 {
     const uint32_t n = *nin;
     const uint32_t lt = gbd::lanemask_lt();
@@ -315,6 +318,7 @@ __global__ void __launch_bounds__(RT) k_select_level(const gblod_node *__restric
             cls = classify(g, fr);
             ccount = g.child_count;
             cfirst = g.child_first;
+            if (cls == 1 && n_parts > 1 && node % n_parts != part) cls = 0;
         }
         // warp-aggregated appends
         const uint32_t em = __ballot_sync(0xffffffffu, cls == 1);
@@ -1699,7 +1703,7 @@ void check_image(const gblod_camera &c)
 }
 
 void render_lod(gblod_renderer *r, const gblod_octree *o, const gblod_camera &cam, const gblod_render_params &rp,
-                uint8_t *image, uint64_t *accum, cudaStream_t s)
+                uint8_t *image, uint64_t *accum, cudaStream_t s, uint32_t part, uint32_t n_parts)
 {
     check_image(cam);
     check_format(o, rp);
@@ -1728,7 +1732,7 @@ void render_lod(gblod_renderer *r, const gblod_octree *o, const gblod_camera &ca
         for (int d = 0; d < levels; ++d) {
             launch(GBLOD_K_SELECT_NODES, k_select_level, dim3(G), dim3(RT), 0, s, nodes, fr,
                    (const uint32_t *)fin, (const uint32_t *)(r->lvl_cnt.p + d), fout, r->lvl_cnt.p + d + 1,
-                   r->sel.p, nsel);
+                   r->sel.p, nsel, part, n_parts);
             std::swap(fin, fout);
         }
     }
@@ -1746,6 +1750,25 @@ void render_lod(gblod_renderer *r, const gblod_octree *o, const gblod_camera &ca
     } else {
         frame_common(r, src, P, rp, image, accum, s);
     }
+}
+
+// R4 alone on a caller's accumulation image (e.g. the sum of the parts of a split frame).
+void tonemap_image(gblod_renderer *r, const uint64_t *accum, int W, int H, const gblod_render_params &rp,
+                   uint8_t *image, cudaStream_t s)
+{
+    const size_t npix = (size_t)W * H;
+    r->maxv.ensure(r->A, 1, s);
+    double lo = 0.0, hi = 0.0;
+    if (rp.tone_auto) {
+        GB_CUDA(cudaMemsetAsync(r->maxv.p, 0, 8, s));
+        launch(GBLOD_K_TONEMAP, k_image_max, dim3(persistent_blocks(2)), dim3(256), 0, s,
+               (const unsigned long long *)accum, npix, r->maxv.p);
+    } else {
+        lo = std::ldexp(rp.tone_lo, 32);
+        hi = std::ldexp(rp.tone_hi, 32);
+    }
+    launch(GBLOD_K_TONEMAP, k_tonemap, dim3(persistent_blocks(2)), dim3(256), 0, s, (const unsigned long long *)accum,
+           npix, (const unsigned long long *)r->maxv.p, rp.tone_auto ? 1 : 0, lo, hi, image);
 }
 
 void render_brute(gblod_renderer *r, const float *xyz, const float *mass, const float *h, uint64_t n,
@@ -1783,7 +1806,8 @@ void morton_keys(const float *xyz, uint64_t n, const double lo[3], double side, 
 // For callers that cannot allocate device memory: the scratch of a brute-force frame lives in one
 // file-scope device array of fixed size, and nothing is allocated per call.  Host code must not
 // pass g_noalloc_scratch itself to a kernel (in host code the name is only a stand-in for the
-// device object); its device address is resolved once per device with cudaGetSymbolAddress.
+// device object); its device address is looked up with cudaGetSymbolAddress in the current device's
+// context on every call.
 namespace gb {
 namespace {
 
@@ -1805,6 +1829,8 @@ constexpr size_t NA_OFF_STATUS = NA_OFF_STATS + na_align(sizeof(FrameStatsDev));
 constexpr size_t NA_OFF_MAXV = NA_OFF_STATUS + na_align(sizeof(unsigned));
 constexpr size_t NA_BYTES = NA_OFF_MAXV + na_align(sizeof(unsigned long long));
 static_assert(NA_BYTES == GBLOD_NOALLOC_SCRATCH_BYTES, "GBLOD_NOALLOC_SCRATCH_BYTES must match the layout");
+// the two scans of NA_TILES counts find their temp space large enough and never allocate
+static_assert(scan_temp_bytes(NA_TILES, sizeof(uint32_t)) <= NA_SCAN_BYTES, "scan temp exceeds its fixed region");
 
 } // namespace
 } // namespace gb
@@ -1814,25 +1840,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[gb::NA_BYTES];
 namespace gb {
 namespace {
 
-constexpr int NA_MAX_DEVICES = 64;
-std::mutex g_na_mu;
-unsigned char *g_na_addr[NA_MAX_DEVICES] = {};
-
-// Device address of g_noalloc_scratch on the current device (resolved once per device).
+// Device address of g_noalloc_scratch in the current device's context, looked up on every call
+// (a lookup is cheap next to a frame, and a cached address would go stale if the context were
+// torn down and created again).
 unsigned char *noalloc_scratch()
 {
-    int dev = 0;
-    GB_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= NA_MAX_DEVICES) fail(GBLOD_ERR_INVALID_ARG, "device ordinal out of range");
-    std::lock_guard<std::mutex> g(g_na_mu);
-    if (!g_na_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        check_cuda(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        if (!p) fail(GBLOD_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
-        g_na_addr[dev] = static_cast<unsigned char *>(p);
-    }
-    return g_na_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    check_cuda(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    if (!p) fail(GBLOD_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
+    return static_cast<unsigned char *>(p);
 }
 
 } // namespace

@@ -44,7 +44,9 @@ namespace gb {
 void renderer_init(gblod_renderer *r, cudaStream_t s);
 void renderer_release(gblod_renderer *r);
 void render_lod(gblod_renderer *r, const gblod_octree *o, const gblod_camera &cam, const gblod_render_params &rp,
-                uint8_t *image, uint64_t *accum, cudaStream_t s);
+                uint8_t *image, uint64_t *accum, cudaStream_t s, uint32_t part = 0, uint32_t n_parts = 1);
+void tonemap_image(gblod_renderer *r, const uint64_t *accum, int W, int H, const gblod_render_params &rp,
+                   uint8_t *image, cudaStream_t s);
 void render_brute(gblod_renderer *r, const float *xyz, const float *mass, const float *h, uint64_t n,
                   const gblod_camera &cam, const gblod_render_params &rp, uint8_t *image, uint64_t *accum,
                   cudaStream_t s);

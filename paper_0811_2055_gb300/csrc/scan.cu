@@ -8,6 +8,7 @@ namespace {
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+static_assert(SCAN_TILE == (int)SCAN_TILE_ELEMS, "scan_temp_bytes assumes this block size");
 
 template <class T> struct Ops;
 
@@ -154,12 +155,7 @@ template <class T>
 void scan_entry(const Allocator &A, ScanTmp &t, const T *in, T *out, size_t n, T *total, cudaStream_t s)
 {
     // worst-case temp: sum over levels of 2 * ceil(n / TILE^k) * sizeof(T) plus alignment slack
-    size_t need = 0, m = n;
-    while (m > (size_t)SCAN_TILE) {
-        m = (m + SCAN_TILE - 1) / SCAN_TILE;
-        need += 2 * m * sizeof(T) + 512;
-    }
-    t.buf.ensure(A, need + 1024, s);
+    t.buf.ensure(A, scan_temp_bytes(n, sizeof(T)), s);
     scan_impl<T>(A, t, in, out, n, total, s, 0);
 }
 

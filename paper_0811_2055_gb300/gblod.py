@@ -114,6 +114,11 @@ _L.gblod_launch_count.restype = _u64
 _L.gblod_probe_enable.argtypes = [_i32]
 _L.gblod_probe_read.argtypes = [C.POINTER(_d), C.POINTER(_u64)]
 _L.gblod_microbench.argtypes = [_i32, C.c_uint32, _vp, C.POINTER(_d), C.POINTER(_d)]
+_L.gblod_octree_node_points.argtypes = [_vp, _u32, _vp, _vp, C.POINTER(_u32), _vp]
+_L.gblod_octree_node_members.argtypes = [_vp, _u32, _vp, C.POINTER(_u32), _vp]
+_L.gblod_octree_set_points.argtypes = [_vp, _u32, _vp, _vp, _u32, _vp]
+_L.gblod_render_part.argtypes = [_vp, _vp, C.POINTER(Camera), C.POINTER(RenderParams), _i32, _i32, _vp, _vp]
+_L.gblod_tonemap.argtypes = [_vp, _vp, _i32, _i32, C.POINTER(RenderParams), _vp, _vp]
 _L.gblod_status_string.restype = C.c_char_p
 _L.gblod_status_string.argtypes = [C.c_int]
 _L.gblod_last_error.restype = C.c_char_p
@@ -122,7 +127,8 @@ for _f in ("gblod_build_lod", "gblod_octree_get_info", "gblod_octree_export", "g
            "gblod_renderer_last_selection", "gblod_morton_keys", "gblod_project", "gblod_probe_enable",
            "gblod_probe_read", "gblod_renderer_reserve_batch", "gblod_render_batch", "gblod_autotune_tiles",
            "gblod_diff_render", "gblod_diff_backward", "gblod_octree_quantize", "gblod_octree_export_block16",
-           "gblod_microbench"):
+           "gblod_microbench", "gblod_render_part", "gblod_tonemap", "gblod_octree_node_points",
+           "gblod_octree_node_members", "gblod_octree_set_points"):
     getattr(_L, _f).restype = C.c_int
 
 
@@ -187,6 +193,36 @@ class Octree:
         i = OctreeInfo()
         _check(_L.gblod_octree_get_info(self._h, C.byref(i)), "gblod_octree_get_info")
         return i
+
+    def node_points(self, node: int, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+        """(count x 4 float32 points x, y, z, weight; count float32 h) stored in `node`, on the device."""
+        n = _u32()
+        _check(_L.gblod_octree_node_points(self._h, int(node), None, None, C.byref(n), _stream(stream)),
+               "gblod_octree_node_points")
+        dev = torch.device("cuda", torch.cuda.current_device())
+        p4 = torch.empty((int(n.value), 4), dtype=torch.float32, device=dev)
+        hs = torch.empty(int(n.value), dtype=torch.float32, device=dev)
+        if n.value:
+            _check(_L.gblod_octree_node_points(self._h, int(node), _ptr(p4), _ptr(hs), C.byref(n), _stream(stream)),
+                   "gblod_octree_node_points")
+        return p4, hs
+
+    def node_members(self, node: int, stream=None) -> torch.Tensor:
+        """Input indices (ids) of the node's member particles, int32 on the device."""
+        n = _u32()
+        _check(_L.gblod_octree_node_members(self._h, int(node), None, C.byref(n), _stream(stream)),
+               "gblod_octree_node_members")
+        ids = torch.empty(int(n.value), dtype=torch.int32, device=torch.device("cuda", torch.cuda.current_device()))
+        if n.value:
+            _check(_L.gblod_octree_node_members(self._h, int(node), _ptr(ids), C.byref(n), _stream(stream)),
+                   "gblod_octree_node_members")
+        return ids
+
+    def set_points(self, node: int, pts4: torch.Tensor, hs: torch.Tensor, stream=None):
+        """Overwrites the node's stored points (gblod_octree_set_points)."""
+        assert pts4.dtype == torch.float32 and hs.dtype == torch.float32 and pts4.shape[1] == 4
+        _check(_L.gblod_octree_set_points(self._h, int(node), _ptr(pts4.contiguous()), _ptr(hs.contiguous()),
+                                          int(pts4.shape[0]), _stream(stream)), "gblod_octree_set_points")
 
     def export(self) -> dict:
         i = self.info()
@@ -262,6 +298,27 @@ class Renderer:
                stream=None):
         """LOD frame; returns (uint8 image or None, int64 accumulator tensor viewed as the u64 image)."""
         return self._frame(octree, None, cam, params, image, accum, stream)
+
+    def render_part(self, octree: Octree, cam: dict, part: int, n_parts: int, params: RenderParams | None = None,
+                    accum=None, stream=None) -> torch.Tensor:
+        """Partial accumulation image of part `part` of `n_parts` of a split frame (gblod_render_part)."""
+        params = params if params is not None else make_params()
+        W, H = int(cam["width"]), int(cam["height"])
+        acc = torch.empty((H, W), dtype=torch.int64, device=torch.device("cuda", torch.cuda.current_device())) \
+            if accum is None else accum
+        c = make_camera(cam)
+        _check(_L.gblod_render_part(self._h, octree.handle, C.byref(c), C.byref(params), int(part), int(n_parts),
+                                    _ptr(acc), _stream(stream)), "gblod_render_part")
+        return acc
+
+    def tonemap(self, accum: torch.Tensor, params: RenderParams | None = None, image=None, stream=None):
+        """8-bit log tone map of an accumulation image (gblod_tonemap)."""
+        params = params if params is not None else make_params()
+        H, W = int(accum.shape[0]), int(accum.shape[1])
+        img = torch.empty((H, W), dtype=torch.uint8, device=accum.device) if image is None else image
+        _check(_L.gblod_tonemap(self._h, _ptr(accum), W, H, C.byref(params), _ptr(img), _stream(stream)),
+               "gblod_tonemap")
+        return img
 
     def render_bruteforce(self, xyz, mass, h, cam: dict, params: RenderParams | None = None, image=True,
                           accum=None, stream=None):

@@ -80,3 +80,43 @@ def test_noalloc_rejects_frames_beyond_its_maximum():
     st = f(xyz.data_ptr(), mass.data_ptr(), h.data_ptr(), p.n, C.addressof(c), C.addressof(params), None, None,
            torch.cuda.current_stream().cuda_stream)
     assert st == gblod.ERR_INVALID_ARG
+
+
+def test_noalloc_rejects_frames_beyond_its_record_maximum_then_still_matches():
+    # a frame within the tile limit that needs more than GBLOD_NOALLOC_MAX_RECORDS (tile, splat)
+    # records: 20,000 blobs of sigma ~ 100 px at 1920 x 1080 touch ~380 tiles each.  The count is
+    # read back on the host before anything is scattered, so the call stops there with
+    # GBLOD_ERR_RANGE; the next good call must still equal the allocating entry point.
+    from paper_0811_2055_gb300 import gblod, synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    f = _entry(gblod.lib())
+    big = synth.uniform(20000, seed=33, h=0.15)
+    cam = synth.look_at((0.5, 0.5, -1.0), (0.5, 0.5, 0.5), width=1920, height=1080)
+    xyz, mass, h = (torch.from_numpy(a).to(dev) for a in (big.xyz, big.mass, big.h))
+    acc = torch.zeros((1080, 1920), dtype=torch.int64, device=dev)
+    c, params = gblod.make_camera(cam), gblod.make_params()
+    stream = torch.cuda.current_stream()
+    st = f(xyz.data_ptr(), mass.data_ptr(), h.data_ptr(), big.n, C.addressof(c), C.addressof(params), None,
+           acc.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    assert st == gblod.ERR_RANGE
+    assert b"fixed maximum" in gblod.lib().gblod_last_error()
+
+    p = synth.tiny(40000, seed=34)
+    small = synth.look_at((0.5, 0.45, -0.8), (0.5, 0.5, 0.5), width=640, height=360)
+    xyz, mass, h = (torch.from_numpy(a).to(dev) for a in (p.xyz, p.mass, p.h))
+    ref = gblod.Renderer()
+    want_img, want_acc = ref.render_bruteforce(xyz, mass, h, small, params)
+    acc = torch.full((360, 640), 99, dtype=torch.int64, device=dev)
+    c = gblod.make_camera(small)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    st = f(xyz.data_ptr(), mass.data_ptr(), h.data_ptr(), p.n, C.addressof(c), C.addressof(params), None,
+           acc.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    assert st == gblod.OK, gblod.lib().gblod_last_error()
+    assert torch.cuda.mem_get_info()[0] == free0  # no device memory taken or kept by the call
+    assert torch.equal(acc, want_acc) and int(acc.count_nonzero()) > 1000
+    ref.close()
