@@ -1116,6 +1116,40 @@ int orc_render_lod(const orc_tree *T, const double lo[3], double side, const orc
     return orc_render_lod_rows(T, lo, side, c, rp, 0, c->height, acc, n_drawn, n_points, NULL);
 }
 
+/* Overwrites the points stored in node `node` with `count` (= its point_count) new ones:
+ * pts4 (x, y, z, weight per point) and hs.  The node's particle bounds and h_cull, and those of
+ * every ancestor, grow to cover the new points (each coordinate or h enters as v + 0, so -0
+ * counts as +0), so that culling stays conservative for what is drawn; the points copy no
+ * particle any more (pt_src = 0xFFFFFFFF).  Returns ORC_OK or ORC_ERR_INVALID. */
+int orc_tree_set_points(orc_tree *T, uint32_t node, const float *pts4, const float *hs, uint64_t count)
+{
+    if (node >= T->n_nodes || count != T->nodes[node].point_count) return ORC_ERR_INVALID;
+    uint64_t pf = T->nodes[node].point_first;
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, hm = -INFINITY;
+    for (uint64_t i = 0; i < count; ++i) {
+        for (int a = 0; a < 4; ++a) T->pts4[4 * (pf + i) + a] = pts4[4 * i + a];
+        T->hs[pf + i] = hs[i];
+        if (T->pt_src) T->pt_src[pf + i] = 0xFFFFFFFFu;
+        for (int a = 0; a < 3; ++a) {
+            float v = pts4[4 * i + a] + 0.0f;
+            if (v < mn[a]) mn[a] = v;
+            if (v > mx[a]) mx[a] = v;
+        }
+        float h = hs[i] + 0.0f;
+        if (h > hm) hm = h;
+    }
+    if (count == 0) return ORC_OK;
+    for (int32_t k = (int32_t)node; k >= 0; k = T->nodes[k].parent) {
+        orc_node *nd = &T->nodes[k];
+        for (int a = 0; a < 3; ++a) {
+            if (mn[a] < nd->bmin[a]) nd->bmin[a] = mn[a];
+            if (mx[a] > nd->bmax[a]) nd->bmax[a] = mx[a];
+        }
+        if (hm > nd->h_cull) nd->h_cull = hm;
+    }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------ 16-bit block codes */
 /* Storage paragraph: every point's position is kept as 2 bytes per coordinate spanning the
  * block (node) that holds it, and the other properties are coded the same way.  Readings:

@@ -125,6 +125,8 @@ def lib():
         L.orc_render_lod_part.argtypes = [P(Tree), f64p, C.c_double, P(Camera), P(RParams), C.c_int32, C.c_int32,
                                           u64p, P(C.c_uint64), P(C.c_uint64)]
         L.orc_render_lod_part.restype = C.c_int
+        L.orc_tree_set_points.argtypes = [P(Tree), C.c_uint32, f32p, f32p, C.c_uint64]
+        L.orc_tree_set_points.restype = C.c_int
         L.orc_render_lod.restype = C.c_int
         L.orc_tonemap.argtypes = [u64p, C.c_uint64, P(RParams), np.ctypeslib.ndpointer(np.uint8, flags="C")]
         L.orc_constants.argtypes = [np.ctypeslib.ndpointer(np.float32, flags="C")]
@@ -274,6 +276,21 @@ class OracleTree:
         if getattr(self, "_ptr", None) is not None and _lib is not None:
             _lib.orc_tree_free(self._ptr)
             self._ptr = None
+
+    def set_points(self, node: int, pts4, hs):
+        """Overwrites node `node`'s stored points (orc_tree_set_points) and refreshes these copies."""
+        pts4 = np.ascontiguousarray(pts4, np.float32).reshape(-1, 4)
+        hs = np.ascontiguousarray(hs, np.float32)
+        st = lib().orc_tree_set_points(self._ptr, int(node), pts4.reshape(-1), hs, pts4.shape[0])
+        if st != OK:
+            raise OracleError(st)
+        T = self._ptr.contents
+        nn, npt = int(T.n_nodes), int(T.n_pts)
+        self.nodes = np.frombuffer(C.string_at(T.nodes, nn * NODE_DTYPE.itemsize), NODE_DTYPE).copy()
+        self.pts4 = np.ctypeslib.as_array(T.pts4, (max(npt, 1) * 4,))[: npt * 4].reshape(npt, 4).copy()
+        self.hs = np.ctypeslib.as_array(T.hs, (max(npt, 1),))[:npt].copy()
+        if T.pt_src:
+            self.pt_src = np.ctypeslib.as_array(T.pt_src, (max(npt, 1),))[:npt].copy()
 
     def masses(self) -> np.ndarray:
         """Exact node masses as Python ints in units of 2^-47."""

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libgblod.so")
 BUILD = os.path.join(HERE, "_build")
-UNITS = ["runtime.cu", "scan.cu", "sort.cu", "build.cu", "select.cu", "render.cu", "diff.cu", "quant.cu", "microbench.cu", "capi.cu"]
+UNITS = ["runtime.cu", "scan.cu", "sort.cu", "build.cu", "select.cu", "render.cu", "diff.cu", "quant.cu", "fit.cu", "microbench.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -182,8 +182,16 @@ def make_params(lambda_px=None, sigma_min_px=0.5, sigma_max_px=128.0, kernel=KER
 class Octree:
     """Device-resident octree built by gblod_build_lod."""
 
-    def __init__(self, handle: int):
+    def __init__(self, handle: int, root_lo=(0.0, 0.0, 0.0), root_side: float = 1.0):
         self._h = handle
+        self.root = (tuple(float(v) for v in root_lo), float(root_side))
+
+    def export_nodes(self) -> np.ndarray:
+        """Host copy of the node table only."""
+        nodes = np.zeros(int(self.info().n_nodes), NODE_DTYPE)
+        _check(_L.gblod_octree_export(self._h, nodes.ctypes.data, None, None, None, None, None),
+               "gblod_octree_export")
+        return nodes
 
     @property
     def handle(self) -> int:
@@ -281,7 +289,7 @@ def build_lod(xyz: torch.Tensor, mass: torch.Tensor, h: torch.Tensor, ids: torch
     _check(_L.gblod_build_lod(_ptr(xyz) if n else None, _ptr(mass) if n else None, _ptr(h) if n else None,
                               _ptr(ids) if ids is not None and n else None, n, C.byref(p), None, _stream(stream),
                               C.byref(out)), "gblod_build_lod")
-    return Octree(out.value)
+    return Octree(out.value, root_lo, root_side)
 
 
 # ------------------------------------------------------------------ rendering

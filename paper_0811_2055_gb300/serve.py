@@ -36,8 +36,8 @@ class Request:
     camera: dict
     ready: float = math.nan
     slot: int = -1
-    checksum: int = 0
-    image: np.ndarray | None = None
+    image: np.ndarray | None = None   # 8-bit image (kept with keep_images)
+    accum: np.ndarray | None = None   # its 64-bit accumulation image (kept with keep_images)
 
 
 @dataclasses.dataclass
@@ -154,7 +154,7 @@ class ServingLoop:
                     rq.ready = tdone
                     if self.keep_images:
                         rq.image = host.numpy().copy()
-                        rq.checksum = int(acc.sum().item())
+                        rq.accum = acc.detach().cpu().numpy().view(np.uint64).copy()
                     self.sessions[rq.session].free_slots.append(rq.slot)
                     rq.slot = -1
                     done.append(rq)

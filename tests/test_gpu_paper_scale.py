@@ -1,7 +1,11 @@
 """The paper-scale timestep (150M particles, the size the paper renders per timestep) at full size:
-properties that hold at any size (node invariants of the octree paragraph; a full-depth LOD frame equal
-to the brute-force frame, bit for bit) and the brute-force image checked pixel by pixel against the
-oracle's direct sum over all 150M particles at a fixed sample of pixels."""
+the device octree equals the oracle's (every node field, the sorted keys and permutation, every
+representative and stored point, bit for bit); the default-detail frames of the whole-box view and of
+the next view in equal the oracle's frames (selection, 64-bit image, 8-bit image within 1), also when
+the frame is split into record-budget passes; properties that hold at any size (node invariants of
+the octree paragraph; a full-depth LOD frame equal to the brute-force frame, bit for bit); and the
+brute-force image checked pixel by pixel against the oracle's direct sum over all 150M particles at a
+fixed sample of pixels."""
 import numpy as np
 import pytest
 import torch
@@ -9,7 +13,7 @@ import torch
 from oracle import oracle as O
 from paper_0811_2055_gb300 import synth
 
-from gpu_helpers import to_dev
+from gpu_helpers import compare_trees, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -25,6 +29,40 @@ def scene():
     t = gblod.build_lod(*d, n_max=N_MAX, seed=1)
     yield gblod, p, d, t
     t.free()
+
+
+@pytest.fixture(scope="module")
+def oracle_tree(scene):
+    G, p, d, t = scene
+    O.set_threads(0)
+    return O.build_tree(p.xyz, p.mass, p.h, seed=1, n_max=N_MAX)
+
+
+def test_octree_equals_the_oracle_at_full_size(scene, oracle_tree):
+    G, p, d, t = scene
+    compare_trees(t.export(), oracle_tree)
+
+
+@pytest.mark.parametrize("view", [7, 6])
+def test_default_detail_frames_equal_the_oracle_at_full_size(scene, oracle_tree, view):
+    G, p, d, t = scene
+    cam = synth.paper_view(view)
+    lam = float(np.sqrt(N_MAX))
+    r = G.Renderer()
+    img, acc = r.render(t, cam, G.make_params(lambda_px=lam))
+    assert r.status() == G.OK
+    sel = r.last_selection()
+    rp = O.rparams(lambda_px=lam)
+    want, st, nd, npts = O.render_lod(oracle_tree, cam, rp)
+    assert st == 0 and nd > 1_000_000
+    assert np.array_equal(sel, O.select(oracle_tree, cam, rp))
+    assert np.array_equal(G.u64(acc), want)
+    assert int(np.abs(img.cpu().numpy().astype(np.int32) - O.tonemap(want, rp).astype(np.int32)).max()) <= 1
+    # the same frame split into passes whose (tile, splat) records fit a small record budget
+    img2, acc2 = r.render(t, cam, G.make_params(lambda_px=lam, record_budget=1 << 23))
+    assert r.status() == G.OK
+    assert torch.equal(acc2, acc) and torch.equal(img2, img)
+    r.close()
 
 
 def test_octree_invariants_at_full_size(scene):

@@ -33,7 +33,7 @@ def _check_alone(gblod, trees, loop, done, k=12):
         rq = done[i]
         img, acc = r.render(trees[rq.timestep], rq.camera, loop.params)
         assert np.array_equal(img.cpu().numpy(), rq.image)
-        assert int(acc.sum().item()) == rq.checksum
+        assert np.array_equal(gblod.u64(acc), rq.accum)  # the 64-bit image, element by element
     r.close()
 
 
