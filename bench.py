@@ -560,8 +560,9 @@ def splat_source(src: bytes) -> bytes:
 # 240-frame mid path given by path_frame, drawn by the census pass), the (tile, splat) records that launch
 # splatted, and the sha256 of the source text above at the time of the capture; the ncu summary under
 # profiles/ lists the same numbers.
-SPLAT_CAPTURE = {"source_sha256": "84df3723180f4af9614404d5e02fe1e2dca24577cac86f10ade50dbcdcdf77e1",
-                 "path_frame": 160, "records": 0, "dram_read_bytes": 444.259840e6, "dram_write_bytes": 16.311552e6}
+SPLAT_CAPTURE = {"source_sha256": "a6e8161f74379157d4278d2cc3894ec8b948030adf41663ed8510e2ab1c41886",
+                 "path_frame": 160, "records": 24527161, "dram_read_bytes": 411.375616e6,
+                 "dram_write_bytes": 16.681216e6}
 
 
 def splat_traffic(records_per_launch: float):
