@@ -661,6 +661,128 @@ __global__ void __launch_bounds__(RT, 4) k_project_scatter(Src src, Proj P, unsi
     if (cstats) count_hits(hits, cstats);
 }
 
+// Partitioned binning for point sources in no spatial order (the caller's particle arrays): the
+// warp-level aggregation of the per-tile counters above finds few equal tiles in a warp there, so
+// every (splat, tile) pair would be one global atomic on one of a few thousand counters.  Instead
+// each CTA of the persistent grid counts its own points per tile in shared memory and writes one
+// histogram, tile-major: hist[t * G + cta].  An exclusive scan of the histograms gives every CTA
+// its own base in every tile, so the scatter pass places records with shared-memory atomics only,
+// and the records of a tile keep the order of the CTAs.  Both passes walk the same chunks (the same
+// grid G and chunk stride), so they see the same points.
+constexpr uint32_t PART_MAX_TILES = 8192; // shared-memory histogram: 32 KB
+
+template <class Src>
+__global__ void __launch_bounds__(RT, 4) k_project_hist(Src src, Proj P, unsigned long long e_lo,
+                                                     unsigned long long e_hi, uint32_t *__restrict__ hist,
+                                                     unsigned *status, FrameStatsDev *stats)
+{
+    extern __shared__ uint32_t sh_cnt[];
+    const uint32_t ntiles = (uint32_t)(P.tiles_x * P.tiles_y);
+    for (uint32_t t = threadIdx.x; t < ntiles; t += RT) sh_cnt[t] = 0u;
+    __syncthreads();
+    const unsigned long long total = min(src_total(src), e_hi);
+    const int lane = threadIdx.x & 31;
+    unsigned long long splats = 0, pairs = 0;
+    AmpSum amp;
+    for (unsigned long long a = e_lo + (unsigned long long)blockIdx.x * CHUNK; a < total;
+         a += (unsigned long long)gridDim.x * CHUNK) {
+        const unsigned long long b = min(total, a + CHUNK);
+        uint32_t j0, j1;
+        src_range(src, a, b, j0, j1);
+        for (unsigned long long e0 = a; e0 < b; e0 += RT) {
+            const unsigned long long e = e0 + threadIdx.x;
+            int res = 0;
+            Splat s;
+            if (e < b) {
+                float x, y, z, w, h;
+                src_load(src, e, j0, j1, x, y, z, w, h);
+                res = project(P, x, y, z, w, h, s);
+            }
+            if (__any_sync(0xffffffffu, res < 0) && lane == 0) atomicOr(status, ST_RANGE);
+            if (res == 1) {
+                amp.add(__float2ull_rn(s.Wf));
+                ++splats;
+                int x0, x1, y0, y1;
+                splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
+                if (x0 <= x1 && y0 <= y1 && !direct_box(x0, x1, y0, y1)) {
+                    const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
+                    pairs += (unsigned long long)(tx1 - tx0 + 1) * (unsigned long long)(ty1 - ty0 + 1);
+                    for (int ty = ty0; ty <= ty1; ++ty)
+                        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&sh_cnt[ty * P.tiles_x + tx], 1u);
+                }
+            }
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        splats += __shfl_xor_sync(0xffffffffu, splats, d);
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, d);
+    }
+    if (lane == 0 && splats) atomicAdd(&stats->splats, splats);
+    if (lane == 0 && pairs) atomicAdd(&stats->pairs, pairs);
+    amp.flush(stats);
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < ntiles; t += RT) hist[(size_t)t * gridDim.x + blockIdx.x] = sh_cnt[t];
+}
+
+// tile counts and offsets from the scanned (tile, CTA) histogram
+__global__ void k_tiles_from_hist(uint32_t ntiles, uint32_t G, const uint32_t *__restrict__ off,
+                                  const uint32_t *total, uint32_t *tile_cnt, uint32_t *tile_off)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const uint32_t a = off[(size_t)t * G], b = t + 1 < ntiles ? off[(size_t)(t + 1) * G] : *total;
+    tile_off[t] = a;
+    tile_cnt[t] = b - a;
+}
+
+// Writes the (tile, point) records of the binned points at this CTA's bases and splats the points
+// with small boxes into img (cstats, if not null, receives the latter's pixel updates).
+template <class Src>
+__global__ void __launch_bounds__(RT, 4) k_project_scatter_part(Src src, Proj P, unsigned long long e_lo,
+                                                             unsigned long long e_hi, const uint32_t *__restrict__ off,
+                                                             uint4 *__restrict__ rec, unsigned long long *img,
+                                                             FrameStatsDev *cstats)
+{
+    extern __shared__ uint32_t sh_cur[];
+    const uint32_t ntiles = (uint32_t)(P.tiles_x * P.tiles_y);
+    for (uint32_t t = threadIdx.x; t < ntiles; t += RT) sh_cur[t] = off[(size_t)t * gridDim.x + blockIdx.x];
+    __syncthreads();
+    const unsigned long long total = min(src_total(src), e_hi);
+    const int32_t *K = g_ktab[P.kernel];
+    unsigned hits = 0;
+    for (unsigned long long a = e_lo + (unsigned long long)blockIdx.x * CHUNK; a < total;
+         a += (unsigned long long)gridDim.x * CHUNK) {
+        const unsigned long long b = min(total, a + CHUNK);
+        uint32_t j0, j1;
+        src_range(src, a, b, j0, j1);
+        for (unsigned long long e0 = a; e0 < b; e0 += RT) {
+            const unsigned long long e = e0 + threadIdx.x;
+            int res = 0;
+            Splat s;
+            if (e < b) {
+                float x, y, z, w, h;
+                src_load(src, e, j0, j1, x, y, z, w, h);
+                res = project(P, x, y, z, w, h, s);
+            }
+            if (res == 1) {
+                int x0, x1, y0, y1;
+                splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
+                if (x0 <= x1 && y0 <= y1) {
+                    if (direct_box(x0, x1, y0, y1)) {
+                        hits += splat_direct(s, x0, x1, y0, y1, K, img, P.W);
+                    } else {
+                        const uint4 r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
+                        const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
+                        for (int ty = ty0; ty <= ty1; ++ty)
+                            for (int tx = tx0; tx <= tx1; ++tx) rec[atomicAdd(&sh_cur[ty * P.tiles_x + tx], 1u)] = r;
+                    }
+                }
+            }
+        }
+    }
+    if (cstats) count_hits(hits, cstats);
+}
+
 __global__ void k_tile_items(uint32_t ntiles, const uint32_t *tile_cnt, uint32_t *item_cnt)
 {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1011,17 +1133,39 @@ struct PassCounts {
     uint32_t items;
 };
 
+// The caller's particle arrays are in no spatial order: they are binned by the partitioned passes
+// (one shared-memory histogram per CTA) whenever the tile count fits shared memory.
+template <class Src> constexpr bool unordered_source() { return false; }
+template <> constexpr bool unordered_source<SrcFlat>() { return true; }
+
+template <class Src> bool partitioned(const Proj &P)
+{
+    return unordered_source<Src>() && (uint32_t)(P.tiles_x * P.tiles_y) <= PART_MAX_TILES;
+}
+
 template <class Src>
 PassCounts bin_count(gblod_renderer *r, const Src &src, const Proj &P, unsigned long long lo, unsigned long long hi,
                      FrameStatsDev *stats, cudaStream_t s)
 {
     const Allocator &A = r->A;
     const uint32_t ntiles = (uint32_t)(P.tiles_x * P.tiles_y);
-    GB_CUDA(cudaMemsetAsync(r->tile_cnt.p, 0, (size_t)ntiles * 4, s));
     const unsigned G = (unsigned)persistent_blocks(4);
-    launch(GBLOD_K_PROJECT_COUNT, k_project_count<Src>, dim3(G), dim3(RT), 0, s, src, P, lo, hi, r->tile_cnt.p,
-           r->status, stats);
-    scan_exclusive_u32(A, r->scan, r->tile_cnt.p, r->tile_off.p, ntiles, r->tile_off.p + ntiles, s);
+    if (partitioned<Src>(P)) {
+        const size_t nh = (size_t)ntiles * G;
+        r->cta_hist.ensure(A, nh, s);
+        r->cta_off.ensure(A, nh + 1, s);
+        launch(GBLOD_K_PROJECT_COUNT, k_project_hist<Src>, dim3(G), dim3(RT), (size_t)ntiles * 4, s, src, P, lo, hi,
+               r->cta_hist.p, r->status, stats);
+        scan_exclusive_u32(A, r->scan, r->cta_hist.p, r->cta_off.p, nh, r->cta_off.p + nh, s);
+        launch(GBLOD_K_RENDER_OTHER, k_tiles_from_hist, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles, G,
+               (const uint32_t *)r->cta_off.p, (const uint32_t *)(r->cta_off.p + nh), r->tile_cnt.p, r->tile_off.p);
+        GB_CUDA(cudaMemcpyAsync(r->tile_off.p + ntiles, r->cta_off.p + nh, 4, cudaMemcpyDeviceToDevice, s));
+    } else {
+        GB_CUDA(cudaMemsetAsync(r->tile_cnt.p, 0, (size_t)ntiles * 4, s));
+        launch(GBLOD_K_PROJECT_COUNT, k_project_count<Src>, dim3(G), dim3(RT), 0, s, src, P, lo, hi, r->tile_cnt.p,
+               r->status, stats);
+        scan_exclusive_u32(A, r->scan, r->tile_cnt.p, r->tile_off.p, ntiles, r->tile_off.p + ntiles, s);
+    }
     launch(GBLOD_K_RENDER_OTHER, k_tile_items, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
            (const uint32_t *)r->tile_cnt.p, r->item_cnt.p);
     scan_exclusive_u32(A, r->scan, r->item_cnt.p, r->item_off.p, ntiles, r->item_off.p + ntiles, s);
@@ -1041,9 +1185,16 @@ void bin_splat(gblod_renderer *r, const Src &src, const Proj &P, unsigned long l
     const uint32_t ntiles = (uint32_t)(P.tiles_x * P.tiles_y);
     r->records.ensure(A, pc.pairs, s);
     r->items.ensure(A, pc.items, s);
-    GB_CUDA(cudaMemcpyAsync(r->tile_cur.p, r->tile_off.p, (size_t)ntiles * 4, cudaMemcpyDeviceToDevice, s));
-    launch(GBLOD_K_PROJECT_SCATTER, k_project_scatter<Src>, dim3((unsigned)persistent_blocks(4)), dim3(RT), 0, s, src,
-           P, lo, hi, r->tile_cur.p, r->records.p, img, r->count_updates ? r->stats : (FrameStatsDev *)nullptr);
+    if (partitioned<Src>(P)) {
+        launch(GBLOD_K_PROJECT_SCATTER, k_project_scatter_part<Src>, dim3((unsigned)persistent_blocks(4)), dim3(RT),
+               (size_t)ntiles * 4, s, src, P, lo, hi, (const uint32_t *)r->cta_off.p, r->records.p, img,
+               r->count_updates ? r->stats : (FrameStatsDev *)nullptr);
+    } else {
+        GB_CUDA(cudaMemcpyAsync(r->tile_cur.p, r->tile_off.p, (size_t)ntiles * 4, cudaMemcpyDeviceToDevice, s));
+        launch(GBLOD_K_PROJECT_SCATTER, k_project_scatter<Src>, dim3((unsigned)persistent_blocks(4)), dim3(RT), 0, s,
+               src, P, lo, hi, r->tile_cur.p, r->records.p, img,
+               r->count_updates ? r->stats : (FrameStatsDev *)nullptr);
+    }
     launch(GBLOD_K_RENDER_OTHER, k_fill_items, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
            (const uint32_t *)r->tile_cnt.p, (const uint32_t *)r->tile_off.p, (const uint32_t *)r->item_off.p,
            r->items.p);
@@ -1678,6 +1829,7 @@ void renderer_release(gblod_renderer *r)
     r->frontA.release(A, s); r->frontB.release(A, s); r->sel.release(A, s); r->lvl_cnt.release(A, s);
     r->sel_pfx.release(A, s); r->sel_base.release(A, s);
     r->tile_cnt.release(A, s); r->tile_off.release(A, s); r->tile_cur.release(A, s);
+    r->cta_hist.release(A, s); r->cta_off.release(A, s);
     r->item_cnt.release(A, s); r->item_off.release(A, s);
     r->records.release(A, s); r->items.release(A, s); r->accum.release(A, s); r->maxv.release(A, s);
     r->pass_stats.release(A, s);
