@@ -47,6 +47,7 @@ def args_():
     ap.add_argument("--no-block16", action="store_true", help="skip the 16-bit block-code fly-through")
     ap.add_argument("--workload", choices=["paper", "mid", "tiny", "diff", "serve", "paper-views"], default="paper")
     ap.add_argument("--view-repeats", type=int, default=4, help="paper: passes over the eight views per step")
+    ap.add_argument("--view-list", type=str, default="", help="paper: comma-separated views (default: all eight)")
     ap.add_argument("--repeats", type=int, default=20, help="paper-views: timed repeats per view")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of offered load")
     ap.add_argument("--sessions", type=int, default=64)
@@ -64,7 +65,7 @@ def args_():
     return ap.parse_args()
 
 
-def workload(name: str, frames: int, particles: int = 0, path_frames: str = ""):
+def workload(name: str, frames: int, particles: int = 0, path_frames: str = "", view_list: str = ""):
     from paper_0811_2055_gb300 import synth
     if name == "mid":
         p = synth.mid(particles) if particles else synth.mid()
@@ -76,8 +77,10 @@ def workload(name: str, frames: int, particles: int = 0, path_frames: str = ""):
                 + "the 240-frame 1920x1080 helical fly-through")
     elif name == "paper":
         p = synth.paper_scale(particles) if particles else synth.paper_scale()
-        cams = [synth.paper_view(j) for j in range(8)]
+        js = [int(x) for x in view_list.split(",") if x.strip()] if view_list else list(range(8))
+        cams = [synth.paper_view(j) for j in js]
         desc = (f"paper: {p.n} particles (65,536 NFW halos + central halo with 30% + 10% uniform), n_max 16000, "
+                + (f"views {view_list} of " if view_list else "") +
                 "the 8 views at 1920x1080 at d_j = 0.01 * 150^(j/7) from inside the central halo out to the whole box")
     else:
         p = synth.tiny()
@@ -169,7 +172,7 @@ def run_ours(a):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    p, views, n_max, desc = workload(a.workload, a.frames, a.particles, a.path_frames)
+    p, views, n_max, desc = workload(a.workload, a.frames, a.particles, a.path_frames, a.view_list)
     reps = max(1, a.view_repeats) if a.workload == "paper" else 1
     cams = [c for _ in range(reps) for c in views]  # the frames of one step
     nv, nf = len(views), len(cams)
@@ -648,7 +651,7 @@ def run_reference(a):
     if rank != 0:
         return
     from oracle import oracle as O
-    p, views, n_max, desc = workload(a.workload, a.frames, a.particles, a.path_frames)
+    p, views, n_max, desc = workload(a.workload, a.frames, a.particles, a.path_frames, a.view_list)
     reps = max(1, a.view_repeats) if a.workload == "paper" else 1
     lam = math.sqrt(n_max)
     cores = _oracle_threads_all()

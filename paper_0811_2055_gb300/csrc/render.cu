@@ -668,17 +668,22 @@ __global__ void __launch_bounds__(RT, 4) k_project_scatter(Src src, Proj P, unsi
 // histogram, tile-major: hist[t * G + cta].  An exclusive scan of the histograms gives every CTA
 // its own base in every tile, so the scatter pass places records with shared-memory atomics only,
 // and the records of a tile keep the order of the CTAs.  Both passes walk the same chunks (the same
-// grid G and chunk stride), so they see the same points.
-constexpr uint32_t PART_MAX_TILES = 8192; // shared-memory histogram: 32 KB
+// grid G and chunk stride), so they see the same points.  Points whose pixel box is at most
+// DIRECT_BOX on a side are binned too, into a second record stream (their own histograms, after the
+// binned points' in the same scan), and splatted by k_splat_small into a shared-memory tile image:
+// in no spatial order, adding them straight to the image would be one global atomic per pixel at
+// random addresses.
+constexpr uint32_t PART_MAX_TILES = 4096; // two shared-memory histograms: 32 KB
+constexpr uint32_t ITEM_SMALL = 4096;     // small records per k_splat_small work item
 
 template <class Src>
 __global__ void __launch_bounds__(RT, 4) k_project_hist(Src src, Proj P, unsigned long long e_lo,
                                                      unsigned long long e_hi, uint32_t *__restrict__ hist,
                                                      unsigned *status, FrameStatsDev *stats)
 {
-    extern __shared__ uint32_t sh_cnt[];
+    extern __shared__ uint32_t sh_cnt[]; // [ntiles] binned points, then [ntiles] small boxes
     const uint32_t ntiles = (uint32_t)(P.tiles_x * P.tiles_y);
-    for (uint32_t t = threadIdx.x; t < ntiles; t += RT) sh_cnt[t] = 0u;
+    for (uint32_t t = threadIdx.x; t < 2 * ntiles; t += RT) sh_cnt[t] = 0u;
     __syncthreads();
     const unsigned long long total = min(src_total(src), e_hi);
     const int lane = threadIdx.x & 31;
@@ -704,11 +709,13 @@ __global__ void __launch_bounds__(RT, 4) k_project_hist(Src src, Proj P, unsigne
                 ++splats;
                 int x0, x1, y0, y1;
                 splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
-                if (x0 <= x1 && y0 <= y1 && !direct_box(x0, x1, y0, y1)) {
+                if (x0 <= x1 && y0 <= y1) {
+                    const bool small = direct_box(x0, x1, y0, y1);
+                    uint32_t *cnt = small ? sh_cnt + ntiles : sh_cnt;
                     const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
-                    pairs += (unsigned long long)(tx1 - tx0 + 1) * (unsigned long long)(ty1 - ty0 + 1);
+                    if (!small) pairs += (unsigned long long)(tx1 - tx0 + 1) * (unsigned long long)(ty1 - ty0 + 1);
                     for (int ty = ty0; ty <= ty1; ++ty)
-                        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&sh_cnt[ty * P.tiles_x + tx], 1u);
+                        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&cnt[ty * P.tiles_x + tx], 1u);
                 }
             }
         }
@@ -721,7 +728,7 @@ __global__ void __launch_bounds__(RT, 4) k_project_hist(Src src, Proj P, unsigne
     if (lane == 0 && pairs) atomicAdd(&stats->pairs, pairs);
     amp.flush(stats);
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < ntiles; t += RT) hist[(size_t)t * gridDim.x + blockIdx.x] = sh_cnt[t];
+    for (uint32_t t = threadIdx.x; t < 2 * ntiles; t += RT) hist[(size_t)t * gridDim.x + blockIdx.x] = sh_cnt[t];
 }
 
 // tile counts and offsets from the scanned (tile, CTA) histogram
@@ -743,13 +750,11 @@ __global__ void __launch_bounds__(RT, 4) k_project_scatter_part(Src src, Proj P,
                                                              uint4 *__restrict__ rec, unsigned long long *img,
                                                              FrameStatsDev *cstats)
 {
-    extern __shared__ uint32_t sh_cur[];
+    extern __shared__ uint32_t sh_cur[]; // [ntiles] binned points, then [ntiles] small boxes
     const uint32_t ntiles = (uint32_t)(P.tiles_x * P.tiles_y);
-    for (uint32_t t = threadIdx.x; t < ntiles; t += RT) sh_cur[t] = off[(size_t)t * gridDim.x + blockIdx.x];
+    for (uint32_t t = threadIdx.x; t < 2 * ntiles; t += RT) sh_cur[t] = off[(size_t)t * gridDim.x + blockIdx.x];
     __syncthreads();
     const unsigned long long total = min(src_total(src), e_hi);
-    const int32_t *K = g_ktab[P.kernel];
-    unsigned hits = 0;
     for (unsigned long long a = e_lo + (unsigned long long)blockIdx.x * CHUNK; a < total;
          a += (unsigned long long)gridDim.x * CHUNK) {
         const unsigned long long b = min(total, a + CHUNK);
@@ -768,19 +773,95 @@ __global__ void __launch_bounds__(RT, 4) k_project_scatter_part(Src src, Proj P,
                 int x0, x1, y0, y1;
                 splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
                 if (x0 <= x1 && y0 <= y1) {
-                    if (direct_box(x0, x1, y0, y1)) {
-                        hits += splat_direct(s, x0, x1, y0, y1, K, img, P.W);
-                    } else {
-                        const uint4 r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
-                        const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
-                        for (int ty = ty0; ty <= ty1; ++ty)
-                            for (int tx = tx0; tx <= tx1; ++tx) rec[atomicAdd(&sh_cur[ty * P.tiles_x + tx], 1u)] = r;
-                    }
+                    uint32_t *cur = direct_box(x0, x1, y0, y1) ? sh_cur + ntiles : sh_cur;
+                    const uint4 r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
+                    const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
+                    for (int ty = ty0; ty <= ty1; ++ty)
+                        for (int tx = tx0; tx <= tx1; ++tx) rec[atomicAdd(&cur[ty * P.tiles_x + tx], 1u)] = r;
                 }
             }
         }
     }
-    if (cstats) count_hits(hits, cstats);
+    (void)img;
+    (void)cstats;
+}
+
+__global__ void k_tile_items_n(uint32_t ntiles, const uint32_t *tile_cnt, uint32_t per_item, uint32_t *item_cnt)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles) item_cnt[t] = (tile_cnt[t] + per_item - 1) / per_item;
+}
+
+__global__ void k_fill_items_n(uint32_t ntiles, const uint32_t *tile_cnt, const uint32_t *tile_off,
+                               const uint32_t *item_off, uint32_t per_item, uint4 *items)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const uint32_t c = tile_cnt[t], o = tile_off[t];
+    uint32_t k = item_off[t];
+    for (uint32_t s = 0; s < c; s += per_item, ++k) items[k] = make_uint4(t, o + s, o + min(c, s + per_item), 0u);
+}
+
+// Small-box records of one work item (a tile and up to ITEM_SMALL of its records): each thread takes
+// records and walks its pixel box clipped to the tile, adding the per-pixel rule's contributions to a
+// shared 64-bit tile image (four copies, one per group of two warps, so that warps adding to the
+// same pixel -- points pile up in dense halo cores -- mostly meet only in the final sum); the copies
+// are then summed and added to the image once per pixel.  The boxes reach at most DIRECT_BOX pixels
+// from the centre, so squared distances fit 32 bits and the table index is the high word of q S
+// shifted by 5.
+template <bool COUNT>
+__global__ void __launch_bounds__(RT) k_splat_small(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
+                                                   Proj P, unsigned long long *__restrict__ img, FrameStatsDev *stats)
+{
+    __shared__ unsigned long long tacc[4][1024]; // TW x TH <= 1024 (checked on the host)
+    __shared__ int32_t K[1024];
+    for (int i = threadIdx.x; i < 1024; i += RT) {
+        K[i] = g_ktab[P.kernel][i];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tacc[c][i] = 0ull;
+    }
+    __syncthreads();
+    unsigned long long *acc = tacc[(threadIdx.x >> 6) & 3];
+    const uint4 it = items[blockIdx.x];
+    const int tx = (int)(it.x % (uint32_t)P.tiles_x), ty = (int)(it.x / (uint32_t)P.tiles_x);
+    const int X0 = tx * P.TW, Y0 = ty * P.TH;
+    const int X1 = min(X0 + P.TW, P.W) - 1, Y1 = min(Y0 + P.TH, P.H) - 1;
+    unsigned hits = 0;
+    for (uint32_t r = it.y + threadIdx.x; r < it.z; r += RT) {
+        const uint4 R = rec[r];
+        const int U = (int)R.x, V = (int)R.y;
+        const uint32_t S = R.z;
+        const unsigned long long Wq = __float2ull_rn(__uint_as_float(R.w));
+        const uint32_t Wh = (uint32_t)(Wq >> 16), Wl = (uint32_t)(Wq & 0xFFFFull);
+        int x0, x1, y0, y1;
+        splat_box(U, V, S, P.W, P.H, x0, x1, y0, y1);
+        x0 = max(x0, X0);
+        x1 = min(x1, X1);
+        y0 = max(y0, Y0);
+        y1 = min(y1, Y1);
+        for (int y = y0; y <= y1; ++y) {
+            const int dy = y * 256 + 128 - V;
+            for (int x = x0; x <= x1; ++x) {
+                const int dx = x * 256 + 128 - U;
+                const uint32_t q = (uint32_t)(dx * dx) + (uint32_t)(dy * dy);
+                const uint32_t idx = __umulhi(q, S) >> 5;
+                if (idx < 1024u) {
+                    const uint32_t kv = (uint32_t)K[idx];
+                    const unsigned long long c = (unsigned long long)Wh * kv + ((Wl * kv) >> 16);
+                    if (c) atomicAdd(&acc[(y - Y0) * P.TW + (x - X0)], c);
+                    if (COUNT) ++hits;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int tw = X1 - X0 + 1, th = Y1 - Y0 + 1;
+    for (int i = threadIdx.x; i < tw * th; i += RT) {
+        const int y = i / tw, x = i - y * tw, k = y * P.TW + x;
+        const unsigned long long v = tacc[0][k] + tacc[1][k] + tacc[2][k] + tacc[3][k];
+        if (v) atomicAdd(&img[(size_t)(Y0 + y) * P.W + (X0 + x)], v);
+    }
+    if (COUNT) count_hits(hits, stats);
 }
 
 __global__ void k_tile_items(uint32_t ntiles, const uint32_t *tile_cnt, uint32_t *item_cnt)
@@ -1129,8 +1210,8 @@ constexpr unsigned long long RECORD_BUDGET_DEFAULT = 1ull << 28; // 4 GiB of rec
 constexpr unsigned long long RECORD_BUDGET_MAX = 1ull << 31;     // offsets stay 32-bit
 
 struct PassCounts {
-    unsigned long long pairs, points;
-    uint32_t items;
+    unsigned long long pairs, points; // records of the pass (both streams when partitioned), points
+    uint32_t items, small_items;      // splat work items, small-box work items (partitioned only)
 };
 
 // The caller's particle arrays are in no spatial order: they are binned by the partitioned passes
@@ -1152,14 +1233,25 @@ PassCounts bin_count(gblod_renderer *r, const Src &src, const Proj &P, unsigned 
     const unsigned G = (unsigned)persistent_blocks(4);
     if (partitioned<Src>(P)) {
         const size_t nh = (size_t)ntiles * G;
-        r->cta_hist.ensure(A, nh, s);
-        r->cta_off.ensure(A, nh + 1, s);
-        launch(GBLOD_K_PROJECT_COUNT, k_project_hist<Src>, dim3(G), dim3(RT), (size_t)ntiles * 4, s, src, P, lo, hi,
+        r->cta_hist.ensure(A, 2 * nh, s);
+        r->cta_off.ensure(A, 2 * nh + 1, s);
+        r->tile_cnt_s.ensure(A, ntiles, s);
+        r->tile_off_s.ensure(A, ntiles + 1, s);
+        r->item_cnt_s.ensure(A, ntiles, s);
+        r->item_off_s.ensure(A, ntiles + 1, s);
+        launch(GBLOD_K_PROJECT_COUNT, k_project_hist<Src>, dim3(G), dim3(RT), (size_t)ntiles * 8, s, src, P, lo, hi,
                r->cta_hist.p, r->status, stats);
-        scan_exclusive_u32(A, r->scan, r->cta_hist.p, r->cta_off.p, nh, r->cta_off.p + nh, s);
-        launch(GBLOD_K_RENDER_OTHER, k_tiles_from_hist, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles, G,
-               (const uint32_t *)r->cta_off.p, (const uint32_t *)(r->cta_off.p + nh), r->tile_cnt.p, r->tile_off.p);
+        scan_exclusive_u32(A, r->scan, r->cta_hist.p, r->cta_off.p, 2 * nh, r->cta_off.p + 2 * nh, s);
+        const dim3 tg((ntiles + 255) / 256);
+        launch(GBLOD_K_RENDER_OTHER, k_tiles_from_hist, tg, dim3(256), 0, s, ntiles, G, (const uint32_t *)r->cta_off.p,
+               (const uint32_t *)(r->cta_off.p + nh), r->tile_cnt.p, r->tile_off.p);
+        launch(GBLOD_K_RENDER_OTHER, k_tiles_from_hist, tg, dim3(256), 0, s, ntiles, G,
+               (const uint32_t *)(r->cta_off.p + nh), (const uint32_t *)(r->cta_off.p + 2 * nh), r->tile_cnt_s.p,
+               r->tile_off_s.p);
         GB_CUDA(cudaMemcpyAsync(r->tile_off.p + ntiles, r->cta_off.p + nh, 4, cudaMemcpyDeviceToDevice, s));
+        launch(GBLOD_K_RENDER_OTHER, k_tile_items_n, tg, dim3(256), 0, s, ntiles, (const uint32_t *)r->tile_cnt_s.p,
+               ITEM_SMALL, r->item_cnt_s.p);
+        scan_exclusive_u32(A, r->scan, r->item_cnt_s.p, r->item_off_s.p, ntiles, r->item_off_s.p + ntiles, s);
     } else {
         GB_CUDA(cudaMemsetAsync(r->tile_cnt.p, 0, (size_t)ntiles * 4, s));
         launch(GBLOD_K_PROJECT_COUNT, k_project_count<Src>, dim3(G), dim3(RT), 0, s, src, P, lo, hi, r->tile_cnt.p,
@@ -1169,12 +1261,20 @@ PassCounts bin_count(gblod_renderer *r, const Src &src, const Proj &P, unsigned 
     launch(GBLOD_K_RENDER_OTHER, k_tile_items, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
            (const uint32_t *)r->tile_cnt.p, r->item_cnt.p);
     scan_exclusive_u32(A, r->scan, r->item_cnt.p, r->item_off.p, ntiles, r->item_off.p + ntiles, s);
-    unsigned long long *h = static_cast<unsigned long long *>(r->hs.get(32));
+    unsigned long long *h = static_cast<unsigned long long *>(r->hs.get(40));
+    h[2] = h[3] = h[4] = 0;
     GB_CUDA(cudaMemcpyAsync(h, &stats->pairs, 8, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaMemcpyAsync(h + 1, &stats->points, 8, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaMemcpyAsync(h + 2, r->item_off.p + ntiles, 4, cudaMemcpyDeviceToHost, s));
+    if (partitioned<Src>(P)) {
+        const size_t nh = (size_t)ntiles * G;
+        GB_CUDA(cudaMemcpyAsync(h + 3, r->item_off_s.p + ntiles, 4, cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaMemcpyAsync(h + 4, r->cta_off.p + 2 * nh, 4, cudaMemcpyDeviceToHost, s));
+    }
     GB_CUDA(cudaStreamSynchronize(s));
-    return PassCounts{h[0], h[1], (uint32_t)(h[2] & 0xFFFFFFFFull)};
+    const bool part = partitioned<Src>(P);
+    return PassCounts{part ? (h[4] & 0xFFFFFFFFull) : h[0], h[1], (uint32_t)(h[2] & 0xFFFFFFFFull),
+                      (uint32_t)(h[3] & 0xFFFFFFFFull)};
 }
 
 template <class Src>
@@ -1184,11 +1284,16 @@ void bin_splat(gblod_renderer *r, const Src &src, const Proj &P, unsigned long l
     const Allocator &A = r->A;
     const uint32_t ntiles = (uint32_t)(P.tiles_x * P.tiles_y);
     r->records.ensure(A, pc.pairs, s);
-    r->items.ensure(A, pc.items, s);
+    r->items.ensure(A, (size_t)pc.items + pc.small_items, s);
     if (partitioned<Src>(P)) {
         launch(GBLOD_K_PROJECT_SCATTER, k_project_scatter_part<Src>, dim3((unsigned)persistent_blocks(4)), dim3(RT),
-               (size_t)ntiles * 4, s, src, P, lo, hi, (const uint32_t *)r->cta_off.p, r->records.p, img,
+               (size_t)ntiles * 8, s, src, P, lo, hi, (const uint32_t *)r->cta_off.p, r->records.p, img,
                r->count_updates ? r->stats : (FrameStatsDev *)nullptr);
+        launch(GBLOD_K_RENDER_OTHER, k_fill_items_n, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
+               (const uint32_t *)r->tile_cnt_s.p, (const uint32_t *)r->tile_off_s.p, (const uint32_t *)r->item_off_s.p,
+               ITEM_SMALL, r->items.p + pc.items);
+        launch(GBLOD_K_SPLAT, r->count_updates ? k_splat_small<true> : k_splat_small<false>, dim3(pc.small_items),
+               dim3(RT), 0, s, (const uint4 *)r->records.p, (const uint4 *)(r->items.p + pc.items), P, img, r->stats);
     } else {
         GB_CUDA(cudaMemcpyAsync(r->tile_cur.p, r->tile_off.p, (size_t)ntiles * 4, cudaMemcpyDeviceToDevice, s));
         launch(GBLOD_K_PROJECT_SCATTER, k_project_scatter<Src>, dim3((unsigned)persistent_blocks(4)), dim3(RT), 0, s,
@@ -1830,6 +1935,7 @@ void renderer_release(gblod_renderer *r)
     r->sel_pfx.release(A, s); r->sel_base.release(A, s);
     r->tile_cnt.release(A, s); r->tile_off.release(A, s); r->tile_cur.release(A, s);
     r->cta_hist.release(A, s); r->cta_off.release(A, s);
+    r->tile_cnt_s.release(A, s); r->tile_off_s.release(A, s); r->item_cnt_s.release(A, s); r->item_off_s.release(A, s);
     r->item_cnt.release(A, s); r->item_off.release(A, s);
     r->records.release(A, s); r->items.release(A, s); r->accum.release(A, s); r->maxv.release(A, s);
     r->pass_stats.release(A, s);

@@ -25,6 +25,7 @@ struct gblod_renderer {
     // R2 / R3
     gb::DBuf<uint32_t> tile_cnt, tile_off, tile_cur, item_cnt, item_off;
     gb::DBuf<uint32_t> cta_hist, cta_off; // partitioned binning: (tile, CTA) counts and their offsets
+    gb::DBuf<uint32_t> tile_cnt_s, tile_off_s, item_cnt_s, item_off_s; // its small-box record stream
     gb::DBuf<uint4> records, items;
     gb::DBuf<unsigned long long> accum, maxv;
     gb::DBuf<gb::FrameStatsDev> pass_stats; // counters of one range when a frame is split
