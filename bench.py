@@ -45,7 +45,8 @@ def args_():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-block16", action="store_true", help="skip the 16-bit block-code fly-through")
-    ap.add_argument("--workload", choices=["paper", "mid", "tiny", "diff", "serve", "paper-views"], default="paper")
+    ap.add_argument("--workload", choices=["paper", "mid", "tiny", "diff", "serve", "paper-views", "fit"], default="paper")
+    ap.add_argument("--fit-steps", type=int, default=40, help="fit: Adam steps per node")
     ap.add_argument("--view-repeats", type=int, default=4, help="paper: passes over the eight views per step")
     ap.add_argument("--view-list", type=str, default="", help="paper: comma-separated views (default: all eight)")
     ap.add_argument("--repeats", type=int, default=20, help="paper-views: timed repeats per view")
@@ -763,6 +764,71 @@ def run_diff(a):
     print(json.dumps(line), flush=True)
 
 
+def run_fit(a):
+    """Visual equivalence of fitted representatives: a 2^22-particle mid-recipe timestep, the internal
+    nodes that eight 1920x1080 views of the fly-through draw are fitted to their particles' images
+    (fit.fit_node: Adam on the adjoint splat, views around each node at the distance it is drawn) and
+    written back; the eight LOD frames are compared with the all-particle frames before and after."""
+    import torch
+
+    from paper_0811_2055_gb300 import fit, gblod, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    p = synth.mid(a.particles or (1 << 22))
+    d = [torch.from_numpy(x).to(dev) for x in (p.xyz, p.mass, p.h)]
+    n_max = 16000
+    lam = math.sqrt(n_max)
+    tree = gblod.build_lod(*d, n_max=n_max, seed=1)
+    r = gblod.Renderer()
+    par = gblod.make_params(lambda_px=lam)
+    cams = [synth.helix_view(k) for k in range(0, 240, 30)]
+    nodes = tree.export_nodes()
+    drawn = set()
+    for cam in cams:
+        r.render(tree, cam, par)
+        drawn |= {int(i) for i in r.last_selection() if nodes[int(i)]["flags"] & gblod.NODE_INTERNAL}
+    full = [r.render_bruteforce(*d, cam, par) for cam in cams]
+
+    def score():
+        out = []
+        for cam, (bi, ba) in zip(cams, full):
+            li, la = r.render(tree, cam, par)
+            dd = (li.int() - bi.int()).double()
+            mse = float((dd * dd).mean())
+            ea = (gblod.u64(la).astype(np.float64) - gblod.u64(ba).astype(np.float64))
+            rel = float(np.sqrt((ea ** 2).sum() / (gblod.u64(ba).astype(np.float64) ** 2).sum()))
+            out.append((10 * math.log10(255.0 ** 2 / mse) if mse > 0 else float("inf"), float(dd.abs().max()), rel))
+        return {"psnr_db_mean": float(np.mean([o[0] for o in out])), "psnr_db_min": float(min(o[0] for o in out)),
+                "max_abs_u8": max(o[1] for o in out), "rel_l2_accum_mean": float(np.mean([o[2] for o in out]))}
+
+    before = score()
+    t0 = time.perf_counter()
+    losses = []
+    for node in sorted(drawn):
+        views = fit.node_views(tree, node, lam, n_views=6, size=128) + \
+            fit.node_views(tree, node, lam, n_views=6, size=128, margin=3.0)
+        res = fit.fit_node(tree, node, *d, views, steps=a.fit_steps, renderer=r)
+        losses.append(res["loss_last"] / max(res["loss_first"], 1e-30))
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    after = score()
+    assert r.status() == gblod.OK
+    line = {"metric": "visual equivalence of LOD frames with fitted representatives: PSNR (dB) of the 8-bit LOD frame "
+                      "against the all-particle frame",
+            "value": after["psnr_db_mean"], "unit": "dB", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 fit, u64 frames",
+            "data": "synthetic",
+            "config": {"workload": f"fit: {p.n} mid-recipe particles, n_max {n_max}, the internal nodes drawn by 8 views "
+                                   "of the 240-frame 1920x1080 fly-through, 12 fit views of 128x128 per node at two distances, "
+                                   "log-intensity L2 loss, "
+                                   f"{a.fit_steps} Adam steps", "nodes_fitted": len(drawn)},
+            "random_subselection": before, "fitted": after, "fit_s": t_fit,
+            "node_loss_ratio_median": float(np.median(losses)) if losses else None}
+    r.close()
+    tree.free()
+    print(json.dumps(line), flush=True)
+
+
 def run_paper_views(a):
     """Paper-scale timestep (150M particles): build, then every one of the eight views at 1920x1080
     and 3840x2160, LOD and all points, each timed `--repeats` times (p50/p99 per view)."""
@@ -914,6 +980,8 @@ def main():
         run_serve(a)
     elif a.workload == "paper-views":
         run_paper_views(a)
+    elif a.workload == "fit":
+        run_fit(a)
     else:
         run_ours(a)
 

@@ -57,42 +57,56 @@ def node_views(tree: gblod.Octree, node: int, lambda_px: float, n_views: int = 8
 
 def fit_node(tree: gblod.Octree, node: int, xyz: torch.Tensor, mass: torch.Tensor, h: torch.Tensor,
              cams: list[dict], steps: int = 60, renderer: gblod.Renderer | None = None,
-             lr_pos: float = 0.02, lr_w: float = 0.02, lr_logh: float = 0.02, write: bool = True) -> dict:
+             lr_pos: float = 0.1, lr_w: float = 0.02, lr_logh: float = 0.02, write: bool = True,
+             log_floor: float | None = 1e-3) -> dict:
     """Fits node `node`'s stored points to the images of its member particles (rows of xyz, mass,
-    h: the arrays the octree was built from).  Learning rates are relative: positions move in units
-    of the node's cell edge, weights and smoothing lengths in log units.  Returns the loss before
-    and after; with `write` the fitted points replace the node's points in the octree."""
+    h: the arrays the octree was built from).  The loss is the L2 difference of log(1 + I / I0) with
+    I0 = log_floor x the brightest target pixel (the display maps intensity logarithmically, so
+    faint and bright regions count alike; log_floor=None: plain intensities).  Learning rates are
+    relative: positions move in units of the points' mean spacing (cell edge / n^(1/3)), weights
+    and smoothing lengths in log units.  The iterate with the lowest loss is kept (the starting
+    points if no step lowered it).  Returns the loss before and after; with `write` the fitted points
+    replace the node's points in the octree (only if they lowered the loss)."""
     r = renderer or gblod.Renderer()
     par = gblod.make_params()
     p4, hs = tree.node_points(node)
     ids = tree.node_members(node).long()
     mx, mm, mh = xyz[ids].contiguous(), mass[ids].contiguous(), h[ids].contiguous()
     target = gblod.diff_render(r, mx, mm, torch.log(mh), cams, par)
-    _, e = node_box(tree, node)
+    i0 = float(target.max()) * log_floor if log_floor else 0.0
+    tmap = (lambda im: torch.log1p(im / i0)) if i0 > 0.0 else (lambda im: im)
+    target = tmap(target)
+    _, edge = node_box(tree, node)
+    e = edge / max(float(p4.shape[0]), 1.0) ** (1.0 / 3.0)  # mean spacing of the node's points
     x0 = p4[:, :3].contiguous()
-    u = torch.zeros_like(x0, requires_grad=True)           # position offset in cell edges
+    u = torch.zeros_like(x0, requires_grad=True)           # position offset in mean spacings
     a = torch.zeros_like(p4[:, 3], requires_grad=True)     # log weight change
     b = torch.zeros_like(hs, requires_grad=True)           # log smoothing-length change
     w0, lh0 = p4[:, 3].contiguous(), torch.log(hs)
     opt = torch.optim.Adam([{"params": [u], "lr": lr_pos}, {"params": [a], "lr": lr_w},
                             {"params": [b], "lr": lr_logh}])
     losses = []
-    for _ in range(steps):
+    best = (float("inf"), None)
+    for _ in range(steps + 1):
         opt.zero_grad()
         img = gblod.SplatImages.apply(x0 + e * u, w0 * torch.exp(a), lh0 + b, cams, r, par)
-        loss = ((img - target) ** 2).sum()
+        loss = ((tmap(torch.clamp(img, min=0.0)) - target) ** 2).sum()
+        lv = float(loss.detach())
+        losses.append(lv)
+        if lv < best[0]:  # the loss of the current iterate, before this step moves it
+            best = (lv, (u.detach().clone(), a.detach().clone(), b.detach().clone()))
+        if len(losses) == steps + 1:
+            break
         loss.backward()
         opt.step()
-        losses.append(float(loss.detach()))
+    bu, ba, bb = best[1]
     with torch.no_grad():
-        img = gblod.diff_render(r, (x0 + e * u).contiguous(), (w0 * torch.exp(a)).contiguous(),
-                                (lh0 + b).contiguous(), cams, par)
-        final = float(((img - target) ** 2).sum())
-        fitted = torch.cat([(x0 + e * u), (w0 * torch.exp(a))[:, None]], 1).contiguous()
-        fh = torch.exp(lh0 + b).contiguous()
-    if write:
+        fitted = torch.cat([(x0 + e * bu), (w0 * torch.exp(ba))[:, None]], 1).contiguous()
+        fh = torch.exp(lh0 + bb).contiguous()
+    improved = best[0] < losses[0]
+    if write and improved:
         tree.set_points(node, fitted, fh)
     if renderer is None:
         r.close()
-    return {"loss_first": losses[0] if losses else final, "loss_last": final, "steps": steps,
+    return {"loss_first": losses[0], "loss_last": best[0], "steps": steps, "improved": improved,
             "points": int(p4.shape[0]), "members": int(ids.numel()), "pts4": fitted, "hs": fh}
