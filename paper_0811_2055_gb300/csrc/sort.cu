@@ -46,19 +46,37 @@ __global__ void __launch_bounds__(RS_THREADS) k_upsweep(const uint64_t *keys, si
     hist[(size_t)d * ntiles + blockIdx.x] = sum;
 }
 
+// Scatter of one tile: keys are ranked stably inside the tile as above, placed in shared memory in
+// the tile's digit order, and then written out by consecutive threads, so that each digit's run of
+// keys (about 16 per tile and digit) goes to consecutive addresses (coalesced stores); values
+// follow through the same buffer.
+struct ScatterSmem {
+    union {
+        uint64_t k[RS_TILE];
+        uint32_t v[RS_TILE];
+    } buf;
+    uint8_t dig[RS_TILE];
+    uint32_t wh[RS_WARPS][256];
+    uint32_t toff[256];
+    uint32_t tstart[256]; // first tile-local position of each digit
+    uint32_t wsum[RS_WARPS];
+};
+static_assert(sizeof(ScatterSmem) <= 48 * 1024, "static shared memory limit");
+
 __global__ void __launch_bounds__(RS_THREADS)
     k_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
               uint32_t *__restrict__ vout, size_t n, int shift, const uint32_t *__restrict__ offs, uint32_t ntiles)
 {
-    __shared__ uint32_t wh[RS_WARPS][256];
-    __shared__ uint32_t toff[256];
+    __shared__ ScatterSmem sm;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wh[0][0])[i] = 0u;
-    toff[threadIdx.x] = offs[(size_t)threadIdx.x * ntiles + blockIdx.x];
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&sm.wh[0][0])[i] = 0u;
+    sm.toff[threadIdx.x] = offs[(size_t)threadIdx.x * ntiles + blockIdx.x];
     __syncthreads();
 
     const uint32_t lt = gbd::lanemask_lt();
-    const size_t base = (size_t)blockIdx.x * RS_TILE + (size_t)warp * (RS_ROUNDS * 32);
+    const size_t tile0 = (size_t)blockIdx.x * RS_TILE;
+    const size_t base = tile0 + (size_t)warp * (RS_ROUNDS * 32);
+    const uint32_t nt = (uint32_t)min((size_t)RS_TILE, n - tile0); // keys in this tile
     uint64_t k[RS_ROUNDS];
     uint32_t v[RS_ROUNDS];
     uint32_t rk[RS_ROUNDS];
@@ -77,32 +95,65 @@ __global__ void __launch_bounds__(RS_THREADS)
         uint32_t tag = ok ? d : (256u + (uint32_t)lane);
         uint32_t peers = __match_any_sync(0xffffffffu, tag);
         uint32_t before = __popc(peers & lt);
-        uint32_t cur = ok ? wh[warp][d] : 0u;
+        uint32_t cur = ok ? sm.wh[warp][d] : 0u;
         rk[r] = cur + before;
         __syncwarp();
-        if (ok && before == 0) wh[warp][d] = cur + __popc(peers);
+        if (ok && before == 0) sm.wh[warp][d] = cur + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
+    uint32_t total; // this thread's digit: keys of the tile with digit threadIdx.x
     {
         uint32_t d = threadIdx.x, run = 0;
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) {
-            uint32_t c = wh[w][d];
-            wh[w][d] = run;
+            uint32_t c = sm.wh[w][d];
+            sm.wh[w][d] = run;
             run += c;
         }
+        total = run;
+    }
+    // exclusive scan of the digit totals over the block: each digit's first tile-local position
+    {
+        uint32_t incl = total;
+        for (int dd = 1; dd < 32; dd <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, dd);
+            if (lane >= dd) incl += o;
+        }
+        if (lane == 31) sm.wsum[warp] = incl;
+        __syncthreads();
+        uint32_t woff = 0;
+        for (int w = 0; w < warp; ++w) woff += sm.wsum[w];
+        sm.tstart[threadIdx.x] = woff + incl - total;
+    }
+    __syncthreads();
+    // keys in tile-local digit order
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        size_t i = base + (size_t)r * 32 + lane;
+        if (i < n) {
+            const uint32_t d = (uint32_t)(k[r] >> shift) & 255u;
+            const uint32_t L = sm.tstart[d] + sm.wh[warp][d] + rk[r];
+            sm.buf.k[L] = k[r];
+            sm.dig[L] = (uint8_t)d;
+            rk[r] = L; // the element's tile-local position, for the values below
+        }
+    }
+    __syncthreads();
+    for (uint32_t L = threadIdx.x; L < nt; L += RS_THREADS) {
+        const uint32_t d = sm.dig[L];
+        kout[(size_t)sm.toff[d] + (L - sm.tstart[d])] = sm.buf.k[L];
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
         size_t i = base + (size_t)r * 32 + lane;
-        if (i < n) {
-            uint32_t d = (uint32_t)(k[r] >> shift) & 255u;
-            uint32_t pos = toff[d] + wh[warp][d] + rk[r];
-            kout[pos] = k[r];
-            vout[pos] = v[r];
-        }
+        if (i < n) sm.buf.v[rk[r]] = v[r];
+    }
+    __syncthreads();
+    for (uint32_t L = threadIdx.x; L < nt; L += RS_THREADS) {
+        const uint32_t d = sm.dig[L];
+        vout[(size_t)sm.toff[d] + (L - sm.tstart[d])] = sm.buf.v[L];
     }
 }
 
