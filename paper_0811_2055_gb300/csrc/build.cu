@@ -41,12 +41,16 @@ __global__ void k_mass_check(const float *mass, size_t n, unsigned *minb, unsign
     }
 }
 
+// pow2: the root cube starts at 0 and scale is a power of two in fp32 range (the fp32 product is exact)
 __global__ void k_morton(const float *__restrict__ xyz, const uint32_t *__restrict__ order, size_t n, double lx,
-                         double ly, double lz, double scale, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals)
+                         double ly, double lz, double scale, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                         int pow2)
 {
+    const float sf = (float)scale;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t src = order ? (size_t)order[i] : i;
-        keys[i] = gbd::morton_key(xyz[3 * src], xyz[3 * src + 1], xyz[3 * src + 2], lx, ly, lz, scale);
+        const float x = xyz[3 * src], y = xyz[3 * src + 1], z = xyz[3 * src + 2];
+        keys[i] = pow2 ? gbd::morton_key_pow2(x, y, z, sf) : gbd::morton_key(x, y, z, lx, ly, lz, scale);
         if (!order) vals[i] = (uint32_t)i;
     }
 }
@@ -64,13 +68,38 @@ __global__ void k_gather_sorted(const float *__restrict__ xyz, const float *__re
                                 const uint32_t *__restrict__ perm, size_t n, float4 *__restrict__ s4,
                                 float *__restrict__ sh, uint32_t *__restrict__ sid, U128 *__restrict__ mfix)
 {
-    for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (size_t)gridDim.x * blockDim.x) {
-        const size_t i = perm[j];
-        const float m = mass[i];
-        s4[j] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], m);
-        sh[j] = h[i];
-        sid[j] = ids ? ids[i] : (uint32_t)i;
-        mfix[j] = gbd::mass_fixed(m);
+    // four independent elements per thread and iteration (each a coalesced sweep of the sorted
+    // order), so that four random reads of the particle arrays are in flight at a time
+    constexpr int GU = 4;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t j0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j0 < n; j0 += stride * GU) {
+        size_t i[GU];
+        float x[GU], y[GU], z[GU], m[GU], hh[GU];
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            const size_t j = j0 + u * stride;
+            i[u] = j < n ? (size_t)perm[j] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            if (j0 + u * stride < n) {
+                x[u] = xyz[3 * i[u]];
+                y[u] = xyz[3 * i[u] + 1];
+                z[u] = xyz[3 * i[u] + 2];
+                m[u] = mass[i[u]];
+                hh[u] = h[i[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            const size_t j = j0 + u * stride;
+            if (j < n) {
+                s4[j] = make_float4(x[u], y[u], z[u], m[u]);
+                sh[j] = hh[u];
+                sid[j] = ids ? ids[i[u]] : (uint32_t)i[u];
+                mfix[j] = gbd::mass_fixed(m[u]);
+            }
+        }
     }
 }
 
@@ -469,6 +498,9 @@ static gblod_octree *build_octree_impl(gblod_octree *o, const float *xyz, const 
     uint64_t *keys = keyA.p;
     uint32_t *vals = valA.p;
     const double scale = 2097152.0 / p.root_side;
+    int sexp = 0;
+    const int pow2 = p.root_lo[0] == 0.0 && p.root_lo[1] == 0.0 && p.root_lo[2] == 0.0 &&
+                     std::frexp(scale, &sexp) == 0.5 && sexp > -120 && sexp < 120 ? 1 : 0;
     if (ids) {
         launch(GBLOD_K_BUILD_OTHER, k_id_keys, dim3(G), dim3(T), 0, s, ids, (size_t)n, keys, vals);
         radix_sort_pairs(A, sort, &keys, &vals, keys == keyA.p ? keyB.p : keyA.p, vals == valA.p ? valB.p : valA.p,
@@ -476,11 +508,11 @@ static gblod_octree *build_octree_impl(gblod_octree *o, const float *xyz, const 
         // vals = input indices in id order; keys in that order
         uint64_t *kdst = keys == keyA.p ? keyB.p : keyA.p;
         launch(GBLOD_K_MORTON, k_morton, dim3(G), dim3(T), 0, s, xyz, (const uint32_t *)vals, (size_t)n, p.root_lo[0],
-               p.root_lo[1], p.root_lo[2], scale, kdst, (uint32_t *)nullptr);
+               p.root_lo[1], p.root_lo[2], scale, kdst, (uint32_t *)nullptr, pow2);
         keys = kdst;
     } else {
         launch(GBLOD_K_MORTON, k_morton, dim3(G), dim3(T), 0, s, xyz, (const uint32_t *)nullptr, (size_t)n,
-               p.root_lo[0], p.root_lo[1], p.root_lo[2], scale, keys, vals);
+               p.root_lo[0], p.root_lo[1], p.root_lo[2], scale, keys, vals, pow2);
     }
     radix_sort_pairs(A, sort, &keys, &vals, keys == keyA.p ? keyB.p : keyA.p, vals == valA.p ? valB.p : valA.p, n, 63,
                      s, hs);

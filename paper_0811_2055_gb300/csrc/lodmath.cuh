@@ -121,6 +121,24 @@ __device__ __forceinline__ uint32_t quantize_axis(float x, double lo, double sca
     return (uint32_t)__double2uint_rz(t);
 }
 
+// The same when the root cube starts at 0 and scale is a power of two (within fp32 range): x * scale
+// is then exact in fp32 (scaling by a power of two; a result below 1 truncates to 0 either way), so
+// the fp32 product gives the identical q without FP64 arithmetic.
+__device__ __forceinline__ uint32_t quantize_axis_pow2(float x, float scale)
+{
+    const float t = __fmul_rn(x, scale);
+    if (!(t >= 0.0f)) return 0u;
+    if (!(t < 2097152.0f)) return 2097151u;
+    return (uint32_t)__float2uint_rz(t);
+}
+
+__device__ __forceinline__ uint64_t morton_key_pow2(float x, float y, float z, float scale)
+{
+    const uint32_t qx = quantize_axis_pow2(x, scale), qy = quantize_axis_pow2(y, scale),
+                   qz = quantize_axis_pow2(z, scale);
+    return (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+}
+
 __device__ __forceinline__ uint64_t morton_key(float x, float y, float z, double lx, double ly, double lz,
                                                double scale)
 {
