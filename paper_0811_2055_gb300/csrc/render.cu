@@ -806,9 +806,9 @@ __global__ void k_fill_items_n(uint32_t ntiles, const uint32_t *tile_cnt, const 
 // records and walks its pixel box clipped to the tile, adding the per-pixel rule's contributions to a
 // shared 64-bit tile image (four copies, one per group of two warps, so that warps adding to the
 // same pixel -- points pile up in dense halo cores -- mostly meet only in the final sum); the copies
-// are then summed and added to the image once per pixel.  The boxes reach at most DIRECT_BOX pixels
-// from the centre, so squared distances fit 32 bits and the table index is the high word of q S
-// shifted by 5.
+// are then summed and added to the image once per pixel.  A box is small once clipped to the image,
+// so its pixels can lie far from a centre outside the image (the visible sliver of a large blob):
+// distances are 64-bit.
 template <bool COUNT>
 __global__ void __launch_bounds__(RT) k_splat_small(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
                                                    Proj P, unsigned long long *__restrict__ img, FrameStatsDev *stats)
@@ -840,12 +840,12 @@ __global__ void __launch_bounds__(RT) k_splat_small(const uint4 *__restrict__ re
         y0 = max(y0, Y0);
         y1 = min(y1, Y1);
         for (int y = y0; y <= y1; ++y) {
-            const int dy = y * 256 + 128 - V;
+            const long long dy = (long long)y * 256 + 128 - V;
             for (int x = x0; x <= x1; ++x) {
-                const int dx = x * 256 + 128 - U;
-                const uint32_t q = (uint32_t)(dx * dx) + (uint32_t)(dy * dy);
-                const uint32_t idx = __umulhi(q, S) >> 5;
-                if (idx < 1024u) {
+                const long long dx = (long long)x * 256 + 128 - U;
+                const unsigned long long q = (unsigned long long)(dx * dx + dy * dy);
+                const unsigned long long idx = (q * (unsigned long long)S) >> 37;
+                if (idx < 1024ull) {
                     const uint32_t kv = (uint32_t)K[idx];
                     const unsigned long long c = (unsigned long long)Wh * kv + ((Wl * kv) >> 16);
                     if (c) atomicAdd(&acc[(y - Y0) * P.TW + (x - X0)], c);

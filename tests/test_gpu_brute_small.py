@@ -1,8 +1,8 @@
 """All-particle frames of unordered particles through the partitioned binning, against the oracle
 bit for bit: mostly tiny splats (the small-box record stream and its shared-memory tile images),
-points stacked on one pixel, points on tile edges and image corners, a frame split into
-record-budget passes, and a frame with more tiles than the partitioned path takes (the ordered
-binning is used there)."""
+points stacked on one pixel, points on tile edges and image corners, large blobs centred off the
+image with a small visible sliver, a frame split into record-budget passes, and a frame with more
+tiles than the partitioned path takes (the ordered binning is used there)."""
 import numpy as np
 import pytest
 import torch
@@ -35,6 +35,15 @@ def test_unordered_all_particle_frames_equal_the_oracle(W, H, budget):
     F, D = cam["f_px"], 1.7
     for k, (u, v) in enumerate([(64.0, 16.0), (0.0, 0.0), (W - 1e-3, H - 1e-3), (128.0, 32.0)]):
         xyz[300 + k] = (0.5 - (u - cam["cx"]) * D / F, 0.5 - (v - cam["cy"]) * D / F, 0.5)
+    # large blobs centred off the image: slivers along an edge, and blobs off a corner whose clipped
+    # box is a few pixels square although its pixels lie hundreds of pixels from the centre (their
+    # disc does not reach the image; a squared distance that wrapped in 32 bits would add spurious
+    # contributions)
+    for k, (u, v, sig) in enumerate([(-296.0, 300.0, 100.0), (W + 296.0, 200.0, 100.0), (500.0, -116.0, 40.0),
+                                     (700.0, H + 116.0, 40.0), (-294.0, -294.0, 100.0), (W + 294.0, -294.0, 100.0),
+                                     (-294.0, H + 294.0, 100.0), (W + 294.0, H + 294.0, 100.0)]):
+        xyz[400 + k] = (0.5 - (u - cam["cx"]) * D / F, 0.5 - (v - cam["cy"]) * D / F, 0.5)
+        h[400 + k] = sig * D / F
     r = gblod.Renderer()
     par = gblod.make_params(record_budget=budget)
     img, acc = r.render_bruteforce(*to_dev(xyz, mass, h), cam, par)
