@@ -59,6 +59,10 @@ void kernel_table_host(int kernel, int32_t *K)
     }
 }
 
+void set_splat_smem_limits();
+
+// once per device: the kernel tables, and the dynamic shared-memory limit of the splat kernels
+// (a device setting, so it is made before any launch that a stream capture could record)
 void ensure_tables()
 {
     static std::mutex mu;
@@ -72,6 +76,7 @@ void ensure_tables()
     kernel_table_host(GBLOD_KERNEL_GAUSSIAN, K[0]);
     kernel_table_host(GBLOD_KERNEL_CUBIC, K[1]);
     GB_CUDA(cudaMemcpyToSymbol(g_ktab, K, sizeof(K)));
+    set_splat_smem_limits();
     done[dev] = 1;
 }
 
@@ -894,7 +899,7 @@ __global__ void k_fill_items(uint32_t ntiles, const uint32_t *tile_cnt, const ui
 constexpr int SPLAT_SLOTS = 4; // 8 warps x 4 blocks of 32 pixels: tiles up to 1024 pixels
 static_assert(ITEM <= (1u << 15), "32-bit partial sums need at most 2^15 records per item");
 
-constexpr int STAGE = 384; // records staged in shared memory at a time
+constexpr int STAGE = 512; // records staged in shared memory at a time (record index: 9 bits)
 
 struct SplatSmem {
     int32_t K[1024];
@@ -907,7 +912,8 @@ struct SplatSmem {
     uint16_t cand[8][STAGE];       // per block column: records whose support may reach it
     uint32_t ncand[2][8];          // candidate counts, two sets used on alternate stages
 };
-static_assert(sizeof(SplatSmem) <= 48 * 1024, "static shared memory limit");
+// dynamic shared memory: four CTAs per SM fit in its 228 KB with the 1 KB each CTA reserves
+static_assert(4 * (sizeof(SplatSmem) + 1024) <= 228 * 1024, "four splat CTAs per SM");
 
 // 16-byte global -> shared copy that bypasses registers and L1 (completes at cp_async_wait_all)
 __device__ __forceinline__ void cp_async16(uint32_t smem_addr, const uint4 *g)
@@ -1043,7 +1049,7 @@ __device__ __forceinline__ void splat_item(const uint4 *__restrict__ rec, const 
         }
         __syncwarp();
         // small records touching all four blocks: no per-block test, four independent chains
-#pragma unroll 2
+#pragma unroll 4
         for (int i = 0; i < nf; ++i) {
             const int j = lst[i] & 511;
             const int4 A = sm.A[j];
@@ -1127,7 +1133,8 @@ __global__ void __launch_bounds__(RT, 4) k_splat_tiles(const uint4 *__restrict__
                                                        Proj P, unsigned long long *__restrict__ img,
                                                        FrameStatsDev *stats)
 {
-    __shared__ SplatSmem sm;
+    extern __shared__ __align__(16) unsigned char splat_smem[];
+    SplatSmem &sm = *reinterpret_cast<SplatSmem *>(splat_smem);
     for (int i = threadIdx.x; i < 1024; i += RT) sm.K[i] = g_ktab[P.kernel][i];
     unsigned hits = 0;
     const uint4 it = items[blockIdx.x];
@@ -1303,8 +1310,8 @@ void bin_splat(gblod_renderer *r, const Src &src, const Proj &P, unsigned long l
     launch(GBLOD_K_RENDER_OTHER, k_fill_items, dim3((ntiles + 255) / 256), dim3(256), 0, s, ntiles,
            (const uint32_t *)r->tile_cnt.p, (const uint32_t *)r->tile_off.p, (const uint32_t *)r->item_off.p,
            r->items.p);
-    launch(GBLOD_K_SPLAT, r->count_updates ? k_splat_tiles<true> : k_splat_tiles<false>, dim3(pc.items), dim3(RT), 0,
-           s, (const uint4 *)r->records.p, (const uint4 *)r->items.p, P, img, r->stats);
+    launch(GBLOD_K_SPLAT, r->count_updates ? k_splat_tiles<true> : k_splat_tiles<false>, dim3(pc.items), dim3(RT),
+           sizeof(SplatSmem), s, (const uint4 *)r->records.p, (const uint4 *)r->items.p, P, img, r->stats);
 }
 
 template <class Src>
@@ -1677,7 +1684,8 @@ __global__ void __launch_bounds__(RT, 4) k_bsplat(const uint4 *__restrict__ rec,
                                                   const ViewDev *__restrict__ views, unsigned *next_item,
                                                   FrameStatsDev *stats)
 {
-    __shared__ SplatSmem sm;
+    extern __shared__ __align__(16) unsigned char splat_smem[];
+    SplatSmem &sm = *reinterpret_cast<SplatSmem *>(splat_smem);
     __shared__ Proj sP;
     __shared__ uint32_t s_item;
     int kernel_loaded = -1;
@@ -1800,6 +1808,16 @@ BatchPlan plan_batch(const gblod_view *views, int n, const gblod_render_params &
     return b;
 }
 
+// the splat kernels stage SplatSmem (above the 48 KB a launch may take without opting in)
+void set_splat_smem_limits()
+{
+    const int bytes = (int)sizeof(SplatSmem);
+    GB_CUDA(cudaFuncSetAttribute(k_splat_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    GB_CUDA(cudaFuncSetAttribute(k_splat_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    GB_CUDA(cudaFuncSetAttribute(k_bsplat<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    GB_CUDA(cudaFuncSetAttribute(k_bsplat<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+}
+
 } // namespace
 
 void reserve_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod_render_params &rp,
@@ -1899,7 +1917,7 @@ void render_batch(gblod_renderer *r, const gblod_view *views, int n, const gblod
            (const FrameStatsDev *)r->stats, r->status);
     // R3: persistent over the items of all views
     launch(GBLOD_K_SPLAT, (rp.flags & GBLOD_RENDER_COUNT_UPDATES) ? k_bsplat<true> : k_bsplat<false>, dim3(G), dim3(RT),
-           0, s, (const uint4 *)r->records.p, (const uint4 *)r->items.p,
+           sizeof(SplatSmem), s, (const uint4 *)r->records.p, (const uint4 *)r->items.p,
            (const uint32_t *)(r->item_off.p + b.ntiles), (uint32_t)items_cap, (const ViewDev *)dv,
            r->lvl_cnt.p + b.max_levels + 2, r->stats);
     // R4
@@ -2181,7 +2199,7 @@ gblod_status render_brute_noalloc(const float *xyz, const float *mass, const flo
     launch(GBLOD_K_RENDER_OTHER, k_fill_items, dim3((nt + 255) / 256), dim3(256), 0, s, nt,
            (const uint32_t *)tile_cnt, (const uint32_t *)tile_off, (const uint32_t *)item_off, items);
     launch(GBLOD_K_SPLAT, (rp.flags & GBLOD_RENDER_COUNT_UPDATES) ? k_splat_tiles<true> : k_splat_tiles<false>,
-           dim3(nitems), dim3(RT), 0, s, (const uint4 *)records, (const uint4 *)items, P, img, stats);
+           dim3(nitems), dim3(RT), sizeof(SplatSmem), s, (const uint4 *)records, (const uint4 *)items, P, img, stats);
     if (image) {
         double lo = 0.0, hi = 0.0;
         if (rp.tone_auto) {
