@@ -151,7 +151,9 @@ __device__ __forceinline__ int project(const Proj &P, float x, float y, float z,
 
 // Pixel box (inclusive) that contains every pixel where the table index can be below 1024:
 // q S < 2^47 needs |d| < sqrt(2^47 / S) in 1/256 px.
-__device__ __forceinline__ void splat_box(int U, int V, uint32_t S, int W, int H, int &x0, int &x1, int &y0, int &y1)
+// Returns the bounding radius r (1/256 px) the box was cut from: every pixel of the box has |dx| <= r
+// and |dy| <= r.
+__device__ __forceinline__ int splat_box(int U, int V, uint32_t S, int W, int H, int &x0, int &x1, int &y0, int &y1)
 {
     const float ql = __fdiv_rn(140737488355328.0f, __uint2float_rn(S));
     const int r = (int)sqrtf(ql) + 2;
@@ -164,6 +166,7 @@ __device__ __forceinline__ void splat_box(int U, int V, uint32_t S, int W, int H
     y0 = max(y0, 0);
     x1 = min(x1, W - 1);
     y1 = min(y1, H - 1);
+    return r;
 }
 
 // Points whose pixel box is at most DIRECT_BOX pixels on a side are not binned: the scatter pass
@@ -201,6 +204,92 @@ __device__ __forceinline__ unsigned splat_direct(const Splat &s, int x0, int x1,
                 const uint32_t kv = (uint32_t)__ldg(&K[idx]);
                 const unsigned long long c = Wh * kv + ((Wl * kv) >> 16);
                 if (c) atomicAdd(&img[(size_t)y * W + x], c);
+                ++hits;
+            }
+        }
+    }
+    return hits;
+}
+
+// Bounding radius (1/256 px) up to which a box's pixels all have q = dx^2 + dy^2 < 2^32 (2 r^2 <
+// 2^32): dx^2 and dy^2 are then signed 32-bit products and the table index (q S) >> 37 is the high
+// word of the 32 x 32 product q S shifted by 5.  Wider boxes (the visible sliver of a large blob
+// centred off the image) take 64-bit distances.
+constexpr int R_NARROW = 46340;
+
+// One point's clipped pixel box for walk_boxes: n pixels (0: none) from origin xy = x0 | y0 << 16,
+// meta = ceil(2^16 / bw) | bw << 17 | wide << 21 for box width bw <= DIRECT_BOX, and the rule's
+// operands U, V, S, Wq = Wh 2^16 + Wl.
+struct BoxWalk {
+    uint32_t n = 0, xy = 0, meta = 0;
+    int U = 0, V = 0;
+    uint32_t S = 0, Wh = 0, Wl = 0;
+};
+
+__device__ __forceinline__ BoxWalk box_walk(int U, int V, uint32_t S, unsigned long long Wq, int r, int x0, int x1,
+                                            int y0, int y1)
+{
+    BoxWalk b;
+    const uint32_t bw = (uint32_t)(x1 - x0 + 1);
+    b.n = bw * (uint32_t)(y1 - y0 + 1);
+    b.xy = (uint32_t)x0 | ((uint32_t)y0 << 16);
+    b.meta = ((65536u + bw - 1u) / bw) | (bw << 17) | (r > R_NARROW ? 1u << 21 : 0u);
+    b.U = U;
+    b.V = V;
+    b.S = S;
+    b.Wh = (uint32_t)(Wq >> 16);
+    b.Wl = (uint32_t)(Wq & 0xFFFFull);
+    return b;
+}
+
+// The per-pixel rule over the boxes (at most DIRECT_BOX x DIRECT_BOX pixels) of a warp's points,
+// one point per lane: the warp walks the concatenation of all lanes' box pixels (row-major within a
+// box) 32 (point, pixel) pairs at a time, pair k on lane k mod 32.  Lanes stay busy whatever the box
+// sizes, and neighbouring lanes take neighbouring pixels of one point instead of 32 points' pixels
+// at the same offset, which in dense regions are often the same pixel.  Row and column of pair m of
+// a box: m / bw = (m ceil(2^16 / bw)) >> 16, exact for m < 2^10.  add(x, y, c) receives every
+// nonzero contribution; returns this lane's pixel updates.  Every lane of the warp calls it.
+template <class Add>
+__device__ __forceinline__ unsigned walk_boxes(const BoxWalk &b, const int32_t *__restrict__ K, Add add)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = b.n;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += o;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t excl = incl - b.n;
+    unsigned hits = 0;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t k = base + (uint32_t)lane;
+        int src = 0; // the last lane whose pixels start at or before k
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t ex = __shfl_sync(0xffffffffu, excl, src + step);
+            if (ex <= k) src += step;
+        }
+        const uint32_t m = k - __shfl_sync(0xffffffffu, excl, src);
+        const uint32_t meta = __shfl_sync(0xffffffffu, b.meta, src), xy = __shfl_sync(0xffffffffu, b.xy, src);
+        const int U = __shfl_sync(0xffffffffu, b.U, src), V = __shfl_sync(0xffffffffu, b.V, src);
+        const uint32_t S = __shfl_sync(0xffffffffu, b.S, src), Wh = __shfl_sync(0xffffffffu, b.Wh, src),
+                       Wl = __shfl_sync(0xffffffffu, b.Wl, src);
+        if (k < total) {
+            const uint32_t bw = (meta >> 17) & 15u;
+            const uint32_t row = (m * (meta & 0x1FFFFu)) >> 16, col = m - row * bw;
+            const int x = (int)(xy & 0xFFFFu) + (int)col, y = (int)(xy >> 16) + (int)row;
+            uint32_t idx;
+            if (!(meta >> 21)) {
+                const int dx = x * 256 + 128 - U, dy = y * 256 + 128 - V;
+                idx = __umulhi((uint32_t)(dx * dx) + (uint32_t)(dy * dy), S) >> 5;
+            } else {
+                const long long dx = (long long)x * 256 + 128 - U, dy = (long long)y * 256 + 128 - V;
+                const unsigned long long i64 = ((unsigned long long)(dx * dx + dy * dy) * S) >> 37;
+                idx = i64 < 1024ull ? (uint32_t)i64 : 1024u;
+            }
+            if (idx < 1024u) {
+                const uint32_t kv = (uint32_t)K[idx];
+                const unsigned long long c = (unsigned long long)Wh * kv + ((Wl * kv) >> 16);
+                if (c) add(x, y, c);
                 ++hits;
             }
         }
@@ -645,12 +734,13 @@ __global__ void __launch_bounds__(RT, 4) k_project_scatter(Src src, Proj P, unsi
             uint32_t n = 0, t00 = 0;
             int tw = 1;
             uint4 r = make_uint4(0u, 0u, 0u, 0u);
+            BoxWalk direct;
             if (res == 1) {
                 int x0, x1, y0, y1;
-                splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
+                const int rad = splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
                 if (x0 <= x1 && y0 <= y1) {
                     if (direct_box(x0, x1, y0, y1)) {
-                        hits += splat_direct(s, x0, x1, y0, y1, K, img, P.W);
+                        direct = box_walk(s.U, s.V, s.S, __float2ull_rn(s.Wf), rad, x0, x1, y0, y1);
                     } else {
                         r = make_uint4((uint32_t)s.U, (uint32_t)s.V, s.S, __float_as_uint(s.Wf));
                         const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
@@ -661,6 +751,9 @@ __global__ void __launch_bounds__(RT, 4) k_project_scatter(Src src, Proj P, unsi
                 }
             }
             scatter_pairs(n, t00, tw, P.tiles_x, r, cursor, rec, ~0ull);
+            hits += walk_boxes(direct, K, [&](int x, int y, unsigned long long c) {
+                atomicAdd(&img[(size_t)y * P.W + x], c);
+            });
         }
     }
     if (cstats) count_hits(hits, cstats);
@@ -807,13 +900,13 @@ __global__ void k_fill_items_n(uint32_t ntiles, const uint32_t *tile_cnt, const 
     for (uint32_t s = 0; s < c; s += per_item, ++k) items[k] = make_uint4(t, o + s, o + min(c, s + per_item), 0u);
 }
 
-// Small-box records of one work item (a tile and up to ITEM_SMALL of its records): each thread takes
-// records and walks its pixel box clipped to the tile, adding the per-pixel rule's contributions to a
-// shared 64-bit tile image (four copies, one per group of two warps, so that warps adding to the
-// same pixel -- points pile up in dense halo cores -- mostly meet only in the final sum); the copies
-// are then summed and added to the image once per pixel.  A box is small once clipped to the image,
-// so its pixels can lie far from a centre outside the image (the visible sliver of a large blob):
-// distances are 64-bit.
+// Small-box records of one work item (a tile and up to ITEM_SMALL of its records): each warp takes
+// 32 records at a time and walks their pixel boxes, clipped to the tile, with walk_boxes, adding the
+// per-pixel rule's contributions to a shared 64-bit tile image (four copies, one per group of two
+// warps, so that warps adding to the same pixel -- points pile up in dense halo cores -- mostly meet
+// only in the final sum); the copies are then summed and added to the image once per pixel.  A box
+// is small once clipped to the image, so its pixels can lie far from a centre outside the image (the
+// visible sliver of a large blob): walk_boxes takes 64-bit distances for those.
 template <bool COUNT>
 __global__ void __launch_bounds__(RT) k_splat_small(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
                                                    Proj P, unsigned long long *__restrict__ img, FrameStatsDev *stats)
@@ -831,33 +924,26 @@ __global__ void __launch_bounds__(RT) k_splat_small(const uint4 *__restrict__ re
     const int tx = (int)(it.x % (uint32_t)P.tiles_x), ty = (int)(it.x / (uint32_t)P.tiles_x);
     const int X0 = tx * P.TW, Y0 = ty * P.TH;
     const int X1 = min(X0 + P.TW, P.W) - 1, Y1 = min(Y0 + P.TH, P.H) - 1;
+    const int TW = P.TW;
     unsigned hits = 0;
-    for (uint32_t r = it.y + threadIdx.x; r < it.z; r += RT) {
-        const uint4 R = rec[r];
-        const int U = (int)R.x, V = (int)R.y;
-        const uint32_t S = R.z;
-        const unsigned long long Wq = __float2ull_rn(__uint_as_float(R.w));
-        const uint32_t Wh = (uint32_t)(Wq >> 16), Wl = (uint32_t)(Wq & 0xFFFFull);
-        int x0, x1, y0, y1;
-        splat_box(U, V, S, P.W, P.H, x0, x1, y0, y1);
-        x0 = max(x0, X0);
-        x1 = min(x1, X1);
-        y0 = max(y0, Y0);
-        y1 = min(y1, Y1);
-        for (int y = y0; y <= y1; ++y) {
-            const long long dy = (long long)y * 256 + 128 - V;
-            for (int x = x0; x <= x1; ++x) {
-                const long long dx = (long long)x * 256 + 128 - U;
-                const unsigned long long q = (unsigned long long)(dx * dx + dy * dy);
-                const unsigned long long idx = (q * (unsigned long long)S) >> 37;
-                if (idx < 1024ull) {
-                    const uint32_t kv = (uint32_t)K[idx];
-                    const unsigned long long c = (unsigned long long)Wh * kv + ((Wl * kv) >> 16);
-                    if (c) atomicAdd(&acc[(y - Y0) * P.TW + (x - X0)], c);
-                    if (COUNT) ++hits;
-                }
-            }
+    for (uint32_t base = it.y + (threadIdx.x & ~31u); base < it.z; base += RT) { // uniform per warp
+        const uint32_t r = base + (threadIdx.x & 31u);
+        BoxWalk b;
+        if (r < it.z) {
+            const uint4 R = rec[r];
+            const int U = (int)R.x, V = (int)R.y;
+            int x0, x1, y0, y1;
+            const int rad = splat_box(U, V, R.z, P.W, P.H, x0, x1, y0, y1);
+            x0 = max(x0, X0);
+            x1 = min(x1, X1);
+            y0 = max(y0, Y0);
+            y1 = min(y1, Y1);
+            if (x0 <= x1 && y0 <= y1)
+                b = box_walk(U, V, R.z, __float2ull_rn(__uint_as_float(R.w)), rad, x0, x1, y0, y1);
         }
+        hits += walk_boxes(b, K, [&](int x, int y, unsigned long long c) {
+            atomicAdd(&acc[(y - Y0) * TW + (x - X0)], c);
+        });
     }
     __syncthreads();
     const int tw = X1 - X0 + 1, th = Y1 - Y0 + 1;
