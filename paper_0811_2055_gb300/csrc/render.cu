@@ -183,34 +183,6 @@ __device__ __forceinline__ bool direct_box(int x0, int x1, int y0, int y1)
     return x1 - x0 < DIRECT_BOX && y1 - y0 < DIRECT_BOX;
 }
 
-// The per-pixel rule for one point over its (clipped) pixel box: q = dx^2 + dy^2 from the pixel
-// centre, index (q S) >> 37, drawn iff the index is below 1024, contribution floor(Wq K / 2^16)
-// (= Wh K + floor(Wl K / 2^16)).  Every pixel of the box lies within the support's bounding radius,
-// so q S < 2^49.  Returns the pixel updates.
-__device__ __forceinline__ unsigned splat_direct(const Splat &s, int x0, int x1, int y0, int y1,
-                                                 const int32_t *__restrict__ K, unsigned long long *img, int W)
-{
-    const unsigned long long Wq = __float2ull_rn(s.Wf);
-    const unsigned long long Wh = Wq >> 16;
-    const uint32_t Wl = (uint32_t)(Wq & 0xFFFFull);
-    unsigned hits = 0;
-    for (int y = y0; y <= y1; ++y) {
-        const long long dy = (long long)y * 256 + 128 - s.V;
-        for (int x = x0; x <= x1; ++x) {
-            const long long dx = (long long)x * 256 + 128 - s.U;
-            const unsigned long long q = (unsigned long long)(dx * dx + dy * dy);
-            const unsigned long long idx = (q * (unsigned long long)s.S) >> 37;
-            if (idx < 1024ull) {
-                const uint32_t kv = (uint32_t)__ldg(&K[idx]);
-                const unsigned long long c = Wh * kv + ((Wl * kv) >> 16);
-                if (c) atomicAdd(&img[(size_t)y * W + x], c);
-                ++hits;
-            }
-        }
-    }
-    return hits;
-}
-
 // Bounding radius (1/256 px) up to which a box's pixels all have q = dx^2 + dy^2 < 2^32 (2 r^2 <
 // 2^32): dx^2 and dy^2 are then signed 32-bit products and the table index (q S) >> 37 is the high
 // word of the 32 x 32 product q S shifted by 5.  Wider boxes (the visible sliver of a large blob
@@ -218,27 +190,28 @@ __device__ __forceinline__ unsigned splat_direct(const Splat &s, int x0, int x1,
 constexpr int R_NARROW = 46340;
 
 // One point's clipped pixel box for walk_boxes: n pixels (0: none) from origin xy = x0 | y0 << 16,
-// meta = ceil(2^16 / bw) | bw << 17 | wide << 21 for box width bw <= DIRECT_BOX, and the rule's
-// operands U, V, S, Wq = Wh 2^16 + Wl.
+// meta = ceil(2^8 / bw) | bw << 9 | wide << 13 | kernel << 14 | Wl << 16 for box width bw <=
+// DIRECT_BOX and the radial kernel's table (0 Gaussian, 1 cubic), and the rule's other operands U,
+// V, S and Wh (Wq = Wh 2^16 + Wl).
 struct BoxWalk {
     uint32_t n = 0, xy = 0, meta = 0;
     int U = 0, V = 0;
-    uint32_t S = 0, Wh = 0, Wl = 0;
+    uint32_t S = 0, Wh = 0;
 };
 
 __device__ __forceinline__ BoxWalk box_walk(int U, int V, uint32_t S, unsigned long long Wq, int r, int x0, int x1,
-                                            int y0, int y1)
+                                            int y0, int y1, int kernel = 0)
 {
     BoxWalk b;
     const uint32_t bw = (uint32_t)(x1 - x0 + 1);
     b.n = bw * (uint32_t)(y1 - y0 + 1);
     b.xy = (uint32_t)x0 | ((uint32_t)y0 << 16);
-    b.meta = ((65536u + bw - 1u) / bw) | (bw << 17) | (r > R_NARROW ? 1u << 21 : 0u);
+    b.meta = ((256u + bw - 1u) / bw) | (bw << 9) | (r > R_NARROW ? 1u << 13 : 0u) | ((uint32_t)kernel << 14) |
+             ((uint32_t)(Wq & 0xFFFFull) << 16);
     b.U = U;
     b.V = V;
     b.S = S;
     b.Wh = (uint32_t)(Wq >> 16);
-    b.Wl = (uint32_t)(Wq & 0xFFFFull);
     return b;
 }
 
@@ -246,11 +219,13 @@ __device__ __forceinline__ BoxWalk box_walk(int U, int V, uint32_t S, unsigned l
 // one point per lane: the warp walks the concatenation of all lanes' box pixels (row-major within a
 // box) 32 (point, pixel) pairs at a time, pair k on lane k mod 32.  Lanes stay busy whatever the box
 // sizes, and neighbouring lanes take neighbouring pixels of one point instead of 32 points' pixels
-// at the same offset, which in dense regions are often the same pixel.  Row and column of pair m of
-// a box: m / bw = (m ceil(2^16 / bw)) >> 16, exact for m < 2^10.  add(x, y, c) receives every
-// nonzero contribution; returns this lane's pixel updates.  Every lane of the warp calls it.
-template <class Add>
-__device__ __forceinline__ unsigned walk_boxes(const BoxWalk &b, const int32_t *__restrict__ K, Add add)
+// at the same offset (in dense regions often the same pixel).  Row and column of pixel m of a box:
+// m / bw = (m ceil(2^8 / bw)) >> 8, exact for m < 64 and bw <= 8.  tab(meta, idx) reads the table
+// entry; add(tag, x, y, c) receives every nonzero contribution with the tag of the point's lane
+// (TAGGED: the lane's `tag`, e.g. its view in a batch; else 0).  Returns this lane's pixel updates.
+// Every lane of the warp calls it.
+template <bool TAGGED, class Tab, class Add>
+__device__ __forceinline__ unsigned walk_boxes(const BoxWalk &b, uint32_t tag, Tab tab, Add add)
 {
     const int lane = threadIdx.x & 31;
     uint32_t incl = b.n;
@@ -271,14 +246,14 @@ __device__ __forceinline__ unsigned walk_boxes(const BoxWalk &b, const int32_t *
         const uint32_t m = k - __shfl_sync(0xffffffffu, excl, src);
         const uint32_t meta = __shfl_sync(0xffffffffu, b.meta, src), xy = __shfl_sync(0xffffffffu, b.xy, src);
         const int U = __shfl_sync(0xffffffffu, b.U, src), V = __shfl_sync(0xffffffffu, b.V, src);
-        const uint32_t S = __shfl_sync(0xffffffffu, b.S, src), Wh = __shfl_sync(0xffffffffu, b.Wh, src),
-                       Wl = __shfl_sync(0xffffffffu, b.Wl, src);
+        const uint32_t S = __shfl_sync(0xffffffffu, b.S, src), Wh = __shfl_sync(0xffffffffu, b.Wh, src);
+        const uint32_t t = TAGGED ? __shfl_sync(0xffffffffu, tag, src) : 0u;
         if (k < total) {
-            const uint32_t bw = (meta >> 17) & 15u;
-            const uint32_t row = (m * (meta & 0x1FFFFu)) >> 16, col = m - row * bw;
+            const uint32_t bw = (meta >> 9) & 15u;
+            const uint32_t row = (m * (meta & 0x1FFu)) >> 8, col = m - row * bw;
             const int x = (int)(xy & 0xFFFFu) + (int)col, y = (int)(xy >> 16) + (int)row;
             uint32_t idx;
-            if (!(meta >> 21)) {
+            if (!(meta & (1u << 13))) {
                 const int dx = x * 256 + 128 - U, dy = y * 256 + 128 - V;
                 idx = __umulhi((uint32_t)(dx * dx) + (uint32_t)(dy * dy), S) >> 5;
             } else {
@@ -287,9 +262,9 @@ __device__ __forceinline__ unsigned walk_boxes(const BoxWalk &b, const int32_t *
                 idx = i64 < 1024ull ? (uint32_t)i64 : 1024u;
             }
             if (idx < 1024u) {
-                const uint32_t kv = (uint32_t)K[idx];
-                const unsigned long long c = (unsigned long long)Wh * kv + ((Wl * kv) >> 16);
-                if (c) add(x, y, c);
+                const uint32_t kv = (uint32_t)tab(meta, idx);
+                const unsigned long long c = (unsigned long long)Wh * kv + (((meta >> 16) * kv) >> 16);
+                if (c) add(t, x, y, c);
                 ++hits;
             }
         }
@@ -751,9 +726,9 @@ __global__ void __launch_bounds__(RT, 4) k_project_scatter(Src src, Proj P, unsi
                 }
             }
             scatter_pairs(n, t00, tw, P.tiles_x, r, cursor, rec, ~0ull);
-            hits += walk_boxes(direct, K, [&](int x, int y, unsigned long long c) {
-                atomicAdd(&img[(size_t)y * P.W + x], c);
-            });
+            hits += walk_boxes<false>(
+                direct, 0u, [&](uint32_t, uint32_t i) { return K[i]; },
+                [&](uint32_t, int x, int y, unsigned long long c) { atomicAdd(&img[(size_t)y * P.W + x], c); });
         }
     }
     if (cstats) count_hits(hits, cstats);
@@ -902,24 +877,34 @@ __global__ void k_fill_items_n(uint32_t ntiles, const uint32_t *tile_cnt, const 
 
 // Small-box records of one work item (a tile and up to ITEM_SMALL of its records): each warp takes
 // 32 records at a time and walks their pixel boxes, clipped to the tile, with walk_boxes, adding the
-// per-pixel rule's contributions to a shared 64-bit tile image (four copies, one per group of two
-// warps, so that warps adding to the same pixel -- points pile up in dense halo cores -- mostly meet
-// only in the final sum); the copies are then summed and added to the image once per pixel.  A box
-// is small once clipped to the image, so its pixels can lie far from a centre outside the image (the
-// visible sliver of a large blob): walk_boxes takes 64-bit distances for those.
+// per-pixel rule's contributions to a shared tile image.  A contribution c < 2^49 is added as three
+// fields, c = lo + mid 2^16 + hi 2^32 with lo, mid < 2^16, to 32-bit words by fire-and-forget
+// 32-bit shared atomics (hi, rarely nonzero, only when it is): a pixel receives at most one
+// contribution per record, so at most ITEM_SMALL = 2^12 per item, and no word can overflow
+// (lo and mid sums < 2^28, hi sums < 2^29).  The lo and mid words have four copies, one per group
+// of two warps, so that warps adding to the same pixel -- points pile up in dense halo cores --
+// mostly meet only in the final sum; the fields are then recombined in 64 bits and added to the
+// image once per pixel.  A box is small once clipped to the image, so its pixels can lie far from a
+// centre outside the image (the visible sliver of a large blob): walk_boxes takes 64-bit distances
+// for those.
+static_assert(ITEM_SMALL <= (1u << 12), "32-bit field sums of the small-box tile image");
 template <bool COUNT>
-__global__ void __launch_bounds__(RT) k_splat_small(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
-                                                   Proj P, unsigned long long *__restrict__ img, FrameStatsDev *stats)
+__global__ void __launch_bounds__(RT, 5) k_splat_small(const uint4 *__restrict__ rec, const uint4 *__restrict__ items,
+                                                      Proj P, unsigned long long *__restrict__ img, FrameStatsDev *stats)
 {
-    __shared__ unsigned long long tacc[4][1024]; // TW x TH <= 1024 (checked on the host)
+    __shared__ uint32_t tlo[4][1024], tmid[4][1024], thi[1024]; // TW x TH <= 1024 (checked on the host)
     __shared__ int32_t K[1024];
     for (int i = threadIdx.x; i < 1024; i += RT) {
         K[i] = g_ktab[P.kernel][i];
+        thi[i] = 0u;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) tacc[c][i] = 0ull;
+        for (int c = 0; c < 4; ++c) {
+            tlo[c][i] = 0u;
+            tmid[c][i] = 0u;
+        }
     }
     __syncthreads();
-    unsigned long long *acc = tacc[(threadIdx.x >> 6) & 3];
+    uint32_t *lo = tlo[(threadIdx.x >> 6) & 3], *mid = tmid[(threadIdx.x >> 6) & 3];
     const uint4 it = items[blockIdx.x];
     const int tx = (int)(it.x % (uint32_t)P.tiles_x), ty = (int)(it.x / (uint32_t)P.tiles_x);
     const int X0 = tx * P.TW, Y0 = ty * P.TH;
@@ -941,15 +926,23 @@ __global__ void __launch_bounds__(RT) k_splat_small(const uint4 *__restrict__ re
             if (x0 <= x1 && y0 <= y1)
                 b = box_walk(U, V, R.z, __float2ull_rn(__uint_as_float(R.w)), rad, x0, x1, y0, y1);
         }
-        hits += walk_boxes(b, K, [&](int x, int y, unsigned long long c) {
-            atomicAdd(&acc[(y - Y0) * TW + (x - X0)], c);
+        hits += walk_boxes<false>(b, 0u, [&](uint32_t, uint32_t i) { return K[i]; },
+                                  [&](uint32_t, int x, int y, unsigned long long c) {
+            const int p = (y - Y0) * TW + (x - X0);
+            atomicAdd(&lo[p], (uint32_t)c & 0xFFFFu);
+            atomicAdd(&mid[p], ((uint32_t)c >> 16));
+            const uint32_t h = (uint32_t)(c >> 32);
+            if (h) atomicAdd(&thi[p], h);
         });
     }
     __syncthreads();
     const int tw = X1 - X0 + 1, th = Y1 - Y0 + 1;
     for (int i = threadIdx.x; i < tw * th; i += RT) {
         const int y = i / tw, x = i - y * tw, k = y * P.TW + x;
-        const unsigned long long v = tacc[0][k] + tacc[1][k] + tacc[2][k] + tacc[3][k];
+        const unsigned long long v =
+            (unsigned long long)tlo[0][k] + tlo[1][k] + tlo[2][k] + tlo[3][k] +
+            (((unsigned long long)tmid[0][k] + tmid[1][k] + tmid[2][k] + tmid[3][k]) << 16) +
+            ((unsigned long long)thi[k] << 32);
         if (v) atomicAdd(&img[(size_t)(Y0 + y) * P.W + (X0 + x)], v);
     }
     if (COUNT) count_hits(hits, stats);
@@ -1692,15 +1685,17 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
             uint32_t n = 0, t00 = 0;
             int tw = 1, tiles_x = 1;
             uint4 r = make_uint4(0u, 0u, 0u, 0u);
+            BoxWalk direct;
             if (res == 1) {
                 const Proj &P = v == sV[0] ? sP[0] : (v == sV[1] ? sP[1] : src.views[v].P);
                 const uint32_t tb = src.views[v].tile_base;
                 if (!SCATTER) ++splats;
                 int x0, x1, y0, y1;
-                splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
+                const int rad = splat_box(s.U, s.V, s.S, P.W, P.H, x0, x1, y0, y1);
                 if (x0 <= x1 && y0 <= y1) {
                     if (direct_box(x0, x1, y0, y1)) {
-                        if (SCATTER) hits += splat_direct(s, x0, x1, y0, y1, g_ktab[P.kernel], src.views[v].accum, P.W);
+                        if (SCATTER)
+                            direct = box_walk(s.U, s.V, s.S, __float2ull_rn(s.Wf), rad, x0, x1, y0, y1, P.kernel);
                     } else {
                         const int tx0 = x0 / P.TW, tx1 = x1 / P.TW, ty0 = y0 / P.TH, ty1 = y1 / P.TH;
                         tw = tx1 - tx0 + 1;
@@ -1714,6 +1709,11 @@ __global__ void __launch_bounds__(RT) k_bproject(SrcBatch src, uint32_t *__restr
             }
             if (SCATTER) {
                 scatter_pairs(n, t00, tw, tiles_x, r, cursor, rec, rec_cap);
+                hits += walk_boxes<true>(
+                    direct, (uint32_t)v, [&](uint32_t meta, uint32_t i) { return g_ktab[(meta >> 14) & 1u][i]; },
+                    [&](uint32_t t, int x, int y, unsigned long long c) {
+                        atomicAdd(&src.views[t].accum[(size_t)y * src.views[t].P.W + x], c);
+                    });
             } else if (n) {
                 // counting: fire-and-forget atomics, so the per-lane loop is cheaper than the
                 // warp-cooperative walk
