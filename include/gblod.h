@@ -48,7 +48,11 @@ typedef enum {
 /* ----------------------------------------------------------------- memory */
 /* Optional allocation hook (e.g. the torch caching allocator).  alloc returns device memory
  * usable on `stream` or NULL; free releases it after the work already enqueued on `stream`.
- * A NULL gblod_allocator* (or NULL alloc) selects cudaMallocAsync / cudaFreeAsync. */
+ * A NULL gblod_allocator* (or NULL alloc) selects the library's own stream-ordered memory pool of
+ * the current device (cudaMallocFromPoolAsync / cudaFreeAsync).  That pool keeps the memory the
+ * library frees mapped, for the library's later allocations (a build frees its sort buffers before
+ * it allocates the sorted arrays; a renderer's buffers and an octree's arrays return to it when
+ * destroyed): it holds at most the library's peak footprint.  gblod_trim_cache returns it. */
 typedef void *(*gblod_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*gblod_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 typedef struct {
@@ -403,6 +407,12 @@ gblod_status gblod_morton_keys(const float *d_xyz, uint64_t n, const double root
  * {drawn (1), culled (0) or out of range (-1), U, V, S, Wq}. */
 gblod_status gblod_project(const float *d_pts4, const float *d_h, uint64_t n, const gblod_camera *camera,
                            const gblod_render_params *params, int64_t *d_out, void *stream);
+
+/* Returns the memory cached by the library's pool of the current device (see gblod_allocator)
+ * to the device, keeping at most keep_bytes; memory still allocated is not touched.  Call it with
+ * no library work in flight on the device that is to free memory (freed blocks are released once
+ * the work before their cudaFreeAsync has completed).  Errors: GBLOD_ERR_CUDA. */
+gblod_status gblod_trim_cache(uint64_t keep_bytes);
 
 /* ----------------------------------------------------------------- instrumentation */
 /* Number of kernel launches this library has issued in the process. */

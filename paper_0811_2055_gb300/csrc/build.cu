@@ -3,6 +3,7 @@
 // the bottom-up cull data.  The subselection (A4/A5) lives in select.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "lodmath.cuh"
 #include "octree.cuh"
@@ -63,10 +64,15 @@ __global__ void k_id_keys(const uint32_t *ids, size_t n, uint64_t *keys, uint32_
     }
 }
 
+// Particles in sorted order: s4 = (x, y, z, m), sh = h, sid = the caller's id (written only when
+// the caller gave ids: otherwise it equals perm), mfix = the fixed-point mass (written only for
+// unequal masses: with one mass m0 for all, a node's exact mass is its count times m0's, and the
+// mass array is not read).
 __global__ void k_gather_sorted(const float *__restrict__ xyz, const float *__restrict__ mass,
                                 const float *__restrict__ h, const uint32_t *__restrict__ ids,
                                 const uint32_t *__restrict__ perm, size_t n, float4 *__restrict__ s4,
-                                float *__restrict__ sh, uint32_t *__restrict__ sid, U128 *__restrict__ mfix)
+                                float *__restrict__ sh, uint32_t *__restrict__ sid, U128 *__restrict__ mfix,
+                                int equal_mass, float m0)
 {
     // four independent elements per thread and iteration (each a coalesced sweep of the sorted
     // order), so that four random reads of the particle arrays are in flight at a time
@@ -86,7 +92,7 @@ __global__ void k_gather_sorted(const float *__restrict__ xyz, const float *__re
                 x[u] = xyz[3 * i[u]];
                 y[u] = xyz[3 * i[u] + 1];
                 z[u] = xyz[3 * i[u] + 2];
-                m[u] = mass[i[u]];
+                m[u] = equal_mass ? m0 : mass[i[u]];
                 hh[u] = h[i[u]];
             }
         }
@@ -96,8 +102,8 @@ __global__ void k_gather_sorted(const float *__restrict__ xyz, const float *__re
             if (j < n) {
                 s4[j] = make_float4(x[u], y[u], z[u], m[u]);
                 sh[j] = hh[u];
-                sid[j] = ids ? ids[i[u]] : (uint32_t)i[u];
-                mfix[j] = gbd::mass_fixed(m[u]);
+                if (sid) sid[j] = ids[i[u]];
+                if (mfix) mfix[j] = gbd::mass_fixed(m[u]);
             }
         }
     }
@@ -197,16 +203,25 @@ __global__ void k_compact_reps(size_t nn, const uint32_t *isrep, const uint32_t 
 }
 
 // Node mass from the exclusive prefix of mass * 2^47; representative weight and h scale.
+// Exact node masses: prefix differences of the fixed-point masses, or (prefix null: one mass m0
+// for every particle) count times m0's fixed-point value.
 __global__ void k_node_mass(size_t nn, size_t n, const uint32_t *first, const uint32_t *count, const uint32_t *flags,
-                            const U128 *prefix, const U128 *total, uint32_t n_max, uint64_t *mlo, uint64_t *mhi,
-                            float *w, float *s)
+                            const U128 *prefix, const U128 *total, float m0, uint32_t n_max, uint64_t *mlo,
+                            uint64_t *mhi, float *w, float *s)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nn) return;
-    const size_t b = first[i], e = b + count[i];
-    const U128 a = prefix[b];
-    const U128 z = e < n ? prefix[e] : *total;
-    const U128 M = gbd::sub128(z, a);
+    U128 M;
+    if (prefix) {
+        const size_t b = first[i], e = b + count[i];
+        const U128 a = prefix[b];
+        const U128 z = e < n ? prefix[e] : *total;
+        M = gbd::sub128(z, a);
+    } else {
+        const U128 f = gbd::mass_fixed(m0); // < 2^71, times a count < 2^32
+        M.lo = f.lo * count[i];
+        M.hi = f.hi * count[i] + __umul64hi(f.lo, (uint64_t)count[i]);
+    }
     mlo[i] = M.lo;
     mhi[i] = M.hi;
     if (flags[i] & FL_REPS) {
@@ -478,6 +493,7 @@ static gblod_octree *build_octree_impl(gblod_octree *o, const float *xyz, const 
     }
     const int T = 256;
     const unsigned G = (unsigned)persistent_blocks(8);
+    float m0 = 0.0f; // the common mass when all are equal
 
     // masses: range and whether they are all equal
     {
@@ -490,6 +506,7 @@ static gblod_octree *build_octree_impl(gblod_octree *o, const float *xyz, const 
         GB_CUDA(cudaStreamSynchronize(s));
         if (hm[2]) fail(GBLOD_ERR_RANGE, "gblod_build_lod: every mass must be finite and in [2^-24, 2^24]");
         o->equal_mass = hm[0] == hm[1] ? 1 : 0;
+        std::memcpy(&m0, &hm[0], sizeof(float));
     }
 
     // A1 + A2: keys in (key, id) order
@@ -525,14 +542,17 @@ static gblod_octree *build_octree_impl(gblod_octree *o, const float *xyz, const 
     o->sidx = sidx;
     keyA.reset(); keyB.reset(); valA.reset(); valB.reset();
 
-    // sorted particle arrays and fixed-point masses
+    // sorted particle arrays and fixed-point masses (with no caller ids the sorted ids are sidx;
+    // with equal masses no prefix of masses is needed)
     Scratch<float4> s4(A, n, s);
     Scratch<float> sh(A, n, s);
-    Scratch<uint32_t> sid(A, n, s);
-    Scratch<U128> mpre(A, n, s), mtot(A, 1, s);
+    Scratch<uint32_t> sid(A, ids ? n : 1, s);
+    Scratch<U128> mpre(A, o->equal_mass ? 1 : n, s), mtot(A, 1, s);
     launch(GBLOD_K_BUILD_OTHER, k_gather_sorted, dim3(G), dim3(T), 0, s, xyz, mass, h, ids, (const uint32_t *)sidx,
-           (size_t)n, s4.p, sh.p, sid.p, mpre.p);
-    scan_exclusive_u128(A, scan, mpre.p, mpre.p, n, mtot.p, s);
+           (size_t)n, s4.p, sh.p, ids ? sid.p : (uint32_t *)nullptr, o->equal_mass ? (U128 *)nullptr : mpre.p,
+           o->equal_mass, m0);
+    if (!o->equal_mass) scan_exclusive_u128(A, scan, mpre.p, mpre.p, n, mtot.p, s);
+    const uint32_t *sorted_ids = ids ? sid.p : sidx;
 
     // A3: node table, one level at a time
     NodeStore &N = tmp.N;
@@ -578,8 +598,9 @@ static gblod_octree *build_octree_impl(gblod_octree *o, const float *xyz, const 
     const uint32_t n_rep = read1(total.p, s, hs);
     o->n_points = npts;
     launch(GBLOD_K_BUILD_OTHER, k_node_mass, dim3(blocks_for(nn, T)), dim3(T), 0, s, nn, (size_t)n,
-           (const uint32_t *)N.first.p, (const uint32_t *)N.count.p, (const uint32_t *)flags.p, (const U128 *)mpre.p,
-           (const U128 *)mtot.p, p.n_max, mlo.p, mhi.p, w.p, sc.p);
+           (const uint32_t *)N.first.p, (const uint32_t *)N.count.p, (const uint32_t *)flags.p,
+           o->equal_mass ? (const U128 *)nullptr : (const U128 *)mpre.p, (const U128 *)mtot.p, m0, p.n_max, mlo.p,
+           mhi.p, w.p, sc.p);
     mpre.reset();
     GB_CUDA(cudaMemsetAsync(hmax.p, 0, nn * sizeof(unsigned), s));
 
@@ -593,7 +614,7 @@ static gblod_octree *build_octree_impl(gblod_octree *o, const float *xyz, const 
         Scratch<uint32_t> reps(A, n_rep, s);
         launch(GBLOD_K_BUILD_OTHER, k_compact_reps, dim3(blocks_for(nn, T)), dim3(T), 0, s, nn,
                (const uint32_t *)isrep.p, (const uint32_t *)reppos.p, reps.p);
-        SelectIn in{s4.p, sh.p, sid.p, N.code.p, N.first.p, N.count.p, pfirst.p, w.p, sc.p, hmax.p,
+        SelectIn in{s4.p, sh.p, sorted_ids, N.code.p, N.first.p, N.count.p, pfirst.p, w.p, sc.p, hmax.p,
                     o->pts4, o->hs, o->pt_src, p.n_max};
         select_representatives(A, s, hs, scan, in, reps.p, n_rep, p.n_max, p.seed, o->equal_mass);
     }

@@ -137,6 +137,7 @@ inline void launch(int kid, void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
 
 int num_sms();
 int persistent_blocks(int per_sm);
+void trim_cache(uint64_t keep_bytes); // unmaps the library pool's cached memory beyond keep_bytes
 
 // ------------------------------------------------------------------ scans (scan.cu)
 // Exclusive prefix sums in place-free form: out[i] = sum_{k<i} in[k]; if total != nullptr the

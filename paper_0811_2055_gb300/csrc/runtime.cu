@@ -13,6 +13,34 @@ static thread_local std::string t_err;
 void set_error(const std::string &msg) { t_err = msg; }
 const char *get_error() { return t_err.c_str(); }
 
+// The library's own stream-ordered memory pool of the current device.  Its release threshold is
+// unbounded: memory freed by the library stays mapped in the pool for its next allocations, so a
+// build that frees its sort buffers and then allocates the sorted particle arrays (and a later build
+// of the same size) reuses mapped memory.  Pools with the default threshold of zero unmap freed
+// memory at every stream synchronisation, and the build synchronises once per octree level.
+// gblod_trim_cache returns the cached memory to the device.
+static cudaMemPool_t lib_pool()
+{
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t mp = nullptr;
+        GB_CUDA(cudaMemPoolCreate(&mp, &props));
+        uint64_t keep = ~0ull;
+        GB_CUDA(cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep));
+        pools[dev] = mp;
+    }
+    return pools[dev];
+}
+
 void *Allocator::get(size_t bytes, cudaStream_t s) const
 {
     if (bytes == 0) bytes = 256;
@@ -22,13 +50,18 @@ void *Allocator::get(size_t bytes, cudaStream_t s) const
         if (!p) fail(GBLOD_ERR_OOM, "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
         return p;
     }
-    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, lib_pool(), s);
     if (e == cudaErrorMemoryAllocation) {
         (void)cudaGetLastError();
-        fail(GBLOD_ERR_OOM, "cudaMallocAsync of " + std::to_string(bytes) + " bytes failed");
+        fail(GBLOD_ERR_OOM, "cudaMallocFromPoolAsync of " + std::to_string(bytes) + " bytes failed");
     }
-    check_cuda(e, "cudaMallocAsync");
+    check_cuda(e, "cudaMallocFromPoolAsync");
     return p;
+}
+
+void trim_cache(uint64_t keep_bytes)
+{
+    GB_CUDA(cudaMemPoolTrimTo(lib_pool(), (size_t)keep_bytes));
 }
 
 void Allocator::put(void *p, size_t bytes, cudaStream_t s) const
@@ -145,6 +178,16 @@ int persistent_blocks(int per_sm) { return num_sms() * per_sm; }
 extern "C" {
 
 uint64_t gblod_launch_count(void) { return gb::g_launches.load(); }
+
+gblod_status gblod_trim_cache(uint64_t keep_bytes)
+{
+    try {
+        gb::trim_cache(keep_bytes);
+        return GBLOD_OK;
+    } catch (const gb::Error &e) {
+        return e.st;
+    }
+}
 
 gblod_status gblod_probe_enable(int32_t kernel)
 {

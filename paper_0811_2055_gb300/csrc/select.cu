@@ -5,7 +5,8 @@
 // Every particle i of node c gets the key k_i = u_i (all masses equal) or the bits of
 // E(u_i)/m_i (exponential race), u_i = Philox(seed; id_i, code_c); the node keeps the n_max
 // smallest (k_i, id_i).  Per node this is a segmented radix select, all nodes at once:
-//   hist     4096-element chunks histogram the top log2(B) key bits (B ~ count/1024 bins)
+//   hist     4096-element chunks histogram the top log2(B) key bits (B ~ count/1024 bins, at
+//            most 4096: a shared-memory histogram per chunk)
 //   find     per node, the bin b that holds rank n_max
 //   mark     keys below bin b set their bit in a per-node bitmap (warp ballots, no atomics);
 //            keys in bin b become candidates (k, id, position)
@@ -48,7 +49,7 @@ __global__ void k_sel_setup(uint32_t n_rep, const uint32_t *nodes, const uint32_
     const uint32_t c = ncount[nodes[r]];
     nchunks[r] = (c + CH - 1) / CH;
     uint32_t want = (c + 1023) / 1024, lb = 0;
-    while (lb < 16 && (1u << lb) < want) ++lb;
+    while (lb < 12 && (1u << lb) < want) ++lb; // at most 4096 bins: the chunk histogram stays in shared memory
     logb[r] = (uint8_t)lb;
     nbins[r] = 1u << lb;
     nwords[r] = (c + 31) / 32;
@@ -109,12 +110,9 @@ __global__ void __launch_bounds__(ST) k_sel_hist(SelectIn in, RepInfo R, uint32_
     __shared__ uint32_t sh[4096];
     ChunkCtx C;
     load_chunk(C, in, R, n_rep);
-    const bool use_shared = C.logb <= 12;
-    const int nb = 1 << C.logb;
-    if (use_shared) {
-        for (int i = threadIdx.x; i < nb; i += ST) sh[i] = 0u;
-        __syncthreads();
-    }
+    const int nb = 1 << C.logb; // <= 4096
+    for (int i = threadIdx.x; i < nb; i += ST) sh[i] = 0u;
+    __syncthreads();
     uint32_t *gh = hist + R.hoff[C.r];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < ROUNDS; ++k) {
@@ -123,17 +121,12 @@ __global__ void __launch_bounds__(ST) k_sel_hist(SelectIn in, RepInfo R, uint32_
             uint32_t id;
             const uint64_t key = sel_key(in, C.first + rel, C.code, seed, equal_mass, id);
             const uint32_t d = C.logb ? (uint32_t)(key >> (64 - C.logb)) : 0u;
-            if (use_shared)
-                atomicAdd(&sh[d], 1u);
-            else
-                atomicAdd(&gh[d], 1u);
+            atomicAdd(&sh[d], 1u);
         }
     }
-    if (use_shared) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < nb; i += ST)
-            if (sh[i]) atomicAdd(&gh[i], sh[i]);
-    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += ST)
+        if (sh[i]) atomicAdd(&gh[i], sh[i]);
 }
 
 // block exclusive scan of one u32 per thread; every thread gets the total

@@ -111,6 +111,7 @@ _L.gblod_diff_render.argtypes = [_vp, _vp, _vp, _vp, _u64, C.POINTER(Camera), _i
 _L.gblod_diff_backward.argtypes = [_vp, _vp, _vp, _vp, _u64, C.POINTER(Camera), _i32, C.POINTER(RenderParams), _vp,
                                    _vp, _vp, _vp, _vp]
 _L.gblod_launch_count.restype = _u64
+_L.gblod_trim_cache.argtypes = [_u64]
 _L.gblod_probe_enable.argtypes = [_i32]
 _L.gblod_probe_read.argtypes = [C.POINTER(_d), C.POINTER(_u64)]
 _L.gblod_microbench.argtypes = [_i32, C.c_uint32, _vp, C.POINTER(_d), C.POINTER(_d)]
@@ -128,7 +129,7 @@ for _f in ("gblod_build_lod", "gblod_octree_get_info", "gblod_octree_export", "g
            "gblod_probe_read", "gblod_renderer_reserve_batch", "gblod_render_batch", "gblod_autotune_tiles",
            "gblod_diff_render", "gblod_diff_backward", "gblod_octree_quantize", "gblod_octree_export_block16",
            "gblod_microbench", "gblod_render_part", "gblod_tonemap", "gblod_octree_node_points",
-           "gblod_octree_node_members", "gblod_octree_set_points"):
+           "gblod_octree_node_members", "gblod_octree_set_points", "gblod_trim_cache"):
     getattr(_L, _f).restype = C.c_int
 
 
@@ -485,6 +486,11 @@ def project(pts4: torch.Tensor, h: torch.Tensor, cam: dict, params: RenderParams
 
 def launch_count() -> int:
     return int(_L.gblod_launch_count())
+
+
+def trim_cache(keep_bytes: int = 0):
+    """Returns the device memory the library's pool keeps cached (beyond keep_bytes) to the device."""
+    _check(_L.gblod_trim_cache(int(keep_bytes)), "gblod_trim_cache")
 
 
 def probe_enable(kernel: int):

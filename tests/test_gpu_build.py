@@ -64,6 +64,21 @@ def test_unequal_masses_outside_points(G):
     compare_trees(t.export(), ot)
 
 
+@pytest.mark.parametrize("m0", [0.3, 3000.0])
+def test_equal_masses_other_than_one_with_and_without_ids(G, m0):
+    # one mass for every particle: node masses are the count times m0's fixed-point value (no mass
+    # prefix), and without caller ids the sorted ids are the sort permutation itself
+    p = synth.clustered(50000, 60, 0.1, 0.3, seed=14)
+    mass = np.full(p.n, m0, np.float32)
+    ids = ((np.arange(p.n, dtype=np.uint64) * 2246822519 + 7) % (1 << 32)).astype(np.uint32)
+    t = G.build_lod(*to_dev(p.xyz, mass, p.h), n_max=200, seed=5)
+    ot = O.build_tree(p.xyz, mass, p.h, seed=5, n_max=200)
+    assert ot.equal_mass
+    compare_trees(t.export(), ot)
+    t = G.build_lod(*to_dev(p.xyz, mass, p.h), ids=to_dev(ids.view(np.int32))[0], n_max=200, seed=5)
+    compare_trees(t.export(), O.build_tree(p.xyz, mass, p.h, ids=ids, seed=5, n_max=200))
+
+
 def test_ids_and_order_freeness(G):
     p = synth.clustered(30000, 40, 0.1, 0.2, seed=6)
     ids = ((np.arange(p.n, dtype=np.uint64) * 2654435761) % (1 << 32)).astype(np.uint32)
