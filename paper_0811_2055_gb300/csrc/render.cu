@@ -219,7 +219,11 @@ __device__ __forceinline__ BoxWalk box_walk(int U, int V, uint32_t S, unsigned l
 // one point per lane: the warp walks the concatenation of all lanes' box pixels (row-major within a
 // box) 32 (point, pixel) pairs at a time, pair k on lane k mod 32.  Lanes stay busy whatever the box
 // sizes, and neighbouring lanes take neighbouring pixels of one point instead of 32 points' pixels
-// at the same offset (in dense regions often the same pixel).  Row and column of pixel m of a box:
+// at the same offset (in dense regions often the same pixel).  The owner of pair k of a window: each
+// lane whose box starts inside the window writes its lane number at its start offset in a per-warp
+// table, one OR-reduction gives the mask of start offsets, and pair k belongs to the box with the
+// last start at or before k (the highest set bit of the mask up to k), or, if none, to the box that
+// owned the previous window's last pair (boxes are contiguous runs of pairs).  Row and column of pixel m of a box:
 // m / bw = (m ceil(2^8 / bw)) >> 8, exact for m < 64 and bw <= 8.  tab(meta, idx) reads the table
 // entry; add(tag, x, y, c) receives every nonzero contribution with the tag of the point's lane
 // (TAGGED: the lane's `tag`, e.g. its view in a batch; else 0).  Returns this lane's pixel updates.
@@ -235,14 +239,20 @@ __device__ __forceinline__ unsigned walk_boxes(const BoxWalk &b, uint32_t tag, T
     }
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     const uint32_t excl = incl - b.n;
+    __shared__ uint8_t owner_at[RT / 32][32];
+    uint8_t *own = owner_at[threadIdx.x >> 5];
     unsigned hits = 0;
+    int carry = 0; // owner of the previous window's last pair
     for (uint32_t base = 0; base < total; base += 32) {
         const uint32_t k = base + (uint32_t)lane;
-        int src = 0; // the last lane whose pixels start at or before k
-        for (int step = 16; step > 0; step >>= 1) {
-            const uint32_t ex = __shfl_sync(0xffffffffu, excl, src + step);
-            if (ex <= k) src += step;
-        }
+        const bool starts = b.n && excl >= base && excl < base + 32u;
+        if (starts) own[excl - base] = (uint8_t)lane;
+        const uint32_t smask = __reduce_or_sync(0xffffffffu, starts ? 1u << (excl - base) : 0u);
+        __syncwarp();
+        const uint32_t upto = smask & (0xffffffffu >> (31 - lane)); // start offsets 0..lane
+        const int src = upto ? (int)own[31 - __clz(upto)] : carry;
+        carry = __shfl_sync(0xffffffffu, src, 31);
+        __syncwarp(); // the table is rewritten in the next window
         const uint32_t m = k - __shfl_sync(0xffffffffu, excl, src);
         const uint32_t meta = __shfl_sync(0xffffffffu, b.meta, src), xy = __shfl_sync(0xffffffffu, b.xy, src);
         const int U = __shfl_sync(0xffffffffu, b.U, src), V = __shfl_sync(0xffffffffu, b.V, src);
