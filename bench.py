@@ -62,7 +62,7 @@ def args_():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-views", type=int, default=16, help="views per batch in the batched measurement")
     ap.add_argument("--batch-capacity-log2", type=int, default=0,
-                    help="log2 of the batch record capacity (0: 30 for paper, 29 otherwise)")
+                    help="log2 of the batch record capacity (0: 31 for paper, 29 otherwise)")
     return ap.parse_args()
 
 
@@ -359,8 +359,9 @@ def run_ours(a):
     if not a.no_batch:
         nbv = max(1, a.batch_views) if a.workload != "paper" else nv
         bcams = views[:: max(1, nv // nbv)][:nbv]
-        # (tile, splat) records, 16 B each (2^29: 8 GiB; the eight paper-scale views take 2^30: 16 GiB)
-        cap = 1 << (a.batch_capacity_log2 or (30 if a.workload == "paper" else 29))
+        # (tile, splat) records, 16 B each (2^29: 8 GiB; the eight paper-scale views need about 1.08e9
+        # with 64x16 tiles, so 2^31: 32 GiB, and fewer with 32x32 tiles, which fit 2^30 but splat slower)
+        cap = 1 << (a.batch_capacity_log2 or (31 if a.workload == "paper" else 29))
         tree = gblod.build_lod(xyz, mass, h, n_max=n_max, seed=1)
         bviews = [(tree, c, torch.empty((H, W), dtype=torch.uint8, device=dev),
                    torch.empty((H, W), dtype=torch.int64, device=dev)) for c in bcams]
