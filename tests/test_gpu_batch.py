@@ -162,3 +162,42 @@ def test_autotuner_picks_a_tile_and_keeps_the_image(G, scene):
         assert torch.equal(acc, ac1)
     alone.close()
     r.close()
+
+
+def test_batch_with_off_image_blobs_and_pixel_piles_matches_the_oracle(G):
+    # Full-depth frames (every leaf particle drawn) of two views of one octree, batched, against the
+    # oracle: points far below a pixel (the small-box walk of the batched projection, pairs tagged
+    # with their view), 2,000 points on one spot, and large blobs centred off each image whose
+    # visible sliver or clipped corner box is small (64-bit distances in the walk).
+    rng = np.random.default_rng(91)
+    n = 40000
+    xyz = rng.uniform(0.0, 1.0, (n, 3)).astype(np.float32)
+    h = np.full(n, 3e-4, np.float32)
+    h[: n // 10] = rng.uniform(0.002, 0.02, n // 10).astype(np.float32)
+    xyz[n // 10: n // 10 + 2000] = (0.5, 0.5, 0.5)
+    mass = np.ones(n, np.float32)
+    cams = [synth.look_at((0.5, 0.5, -1.2), (0.5, 0.5, 0.5), width=640, height=360),
+            synth.look_at((0.5, 0.5, -1.2), (0.5, 0.5, 0.5), width=333, height=197)]
+    D = 1.7
+    for j, cam in enumerate(cams):
+        W, H, F = cam["width"], cam["height"], cam["f_px"]
+        for k, (u, v, sig) in enumerate([(-296.0, 100.0, 100.0), (W + 296.0, 50.0, 100.0), (-294.0, -294.0, 100.0),
+                                         (W + 294.0, H + 294.0, 100.0), (100.0, -116.0, 40.0)]):
+            xyz[500 + 10 * j + k] = (0.5 - (u - cam["cx"]) * D / F, 0.5 - (v - cam["cy"]) * D / F, 0.5)
+            h[500 + 10 * j + k] = sig * D / F
+    t = G.build_lod(*to_dev(xyz, mass, h), n_max=500, seed=4)
+    dev = torch.device("cuda", 0)
+    views = _views(dev, [(t, cams[0]), (t, cams[1])])
+    r = G.Renderer()
+    par = G.make_params(lambda_px=0.0)
+    r.reserve_batch(views, par, record_capacity=1 << 22)
+    r.render_batch(views, par)
+    torch.cuda.synchronize()
+    assert r.status() == G.OK
+    ot = O.build_tree(xyz, mass, h, seed=4, n_max=500)
+    for _, cam, img, acc in views:
+        want, st, _, _ = O.render_lod(ot, cam, O.rparams(lambda_px=0.0))
+        assert st == 0 and int(want.max()) > 0
+        assert np.array_equal(G.u64(acc), want)
+    r.close()
+    t.free()
