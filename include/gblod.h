@@ -48,11 +48,12 @@ typedef enum {
 /* ----------------------------------------------------------------- memory */
 /* Optional allocation hook (e.g. the torch caching allocator).  alloc returns device memory
  * usable on `stream` or NULL; free releases it after the work already enqueued on `stream`.
- * A NULL gblod_allocator* (or NULL alloc) selects the library's own stream-ordered memory pool of
- * the current device (cudaMallocFromPoolAsync / cudaFreeAsync).  That pool keeps the memory the
- * library frees mapped, for the library's later allocations (a build frees its sort buffers before
- * it allocates the sorted arrays; a renderer's buffers and an octree's arrays return to it when
- * destroyed): it holds at most the library's peak footprint.  gblod_trim_cache returns it. */
+ * A NULL gblod_allocator* (or NULL alloc) selects, for builds and octrees, the library's own
+ * stream-ordered memory pool of the current device (cudaMallocFromPoolAsync / cudaFreeAsync), and,
+ * for renderers (grow-only buffers), cudaMallocAsync / cudaFreeAsync on the device's default pool.
+ * The library's pool keeps the memory freed into it mapped, for the next builds (a build frees its
+ * sort buffers before it allocates the sorted arrays; an octree's arrays return to it when freed):
+ * it holds at most the builds' peak footprint.  gblod_trim_cache returns it. */
 typedef void *(*gblod_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*gblod_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 typedef struct {

@@ -193,7 +193,7 @@ gblod_status gblod_renderer_create(const gblod_allocator *alloc, gblod_renderer 
     return guarded([&] {
         if (!out) fail(GBLOD_ERR_INVALID_ARG, "out is NULL");
         gblod_renderer *r = new gblod_renderer();
-        r->A = Allocator(alloc);
+        r->A = Allocator(alloc, false); // grow-only buffers: the default stream-ordered pool
         try {
             renderer_init(r, nullptr);
         } catch (...) {

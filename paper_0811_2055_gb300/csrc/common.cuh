@@ -40,7 +40,8 @@ inline void fail(gblod_status s, const std::string &msg)
 struct Allocator {
     gblod_allocator hook{};
     bool has_hook = false;
-    explicit Allocator(const gblod_allocator *a = nullptr)
+    bool pooled = true; // without a hook: the library's retaining pool (else cudaMallocAsync's default pool)
+    explicit Allocator(const gblod_allocator *a = nullptr, bool use_pool = true) : pooled(use_pool)
     {
         if (a && a->alloc && a->free) {
             hook = *a;

@@ -50,12 +50,12 @@ void *Allocator::get(size_t bytes, cudaStream_t s) const
         if (!p) fail(GBLOD_ERR_OOM, "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
         return p;
     }
-    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, lib_pool(), s);
+    cudaError_t e = pooled ? cudaMallocFromPoolAsync(&p, bytes, lib_pool(), s) : cudaMallocAsync(&p, bytes, s);
     if (e == cudaErrorMemoryAllocation) {
         (void)cudaGetLastError();
-        fail(GBLOD_ERR_OOM, "cudaMallocFromPoolAsync of " + std::to_string(bytes) + " bytes failed");
+        fail(GBLOD_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
     }
-    check_cuda(e, "cudaMallocFromPoolAsync");
+    check_cuda(e, pooled ? "cudaMallocFromPoolAsync" : "cudaMallocAsync");
     return p;
 }
 
